@@ -1,0 +1,360 @@
+"""Benchmark of the CSGD / GCSGD block solver on GB300.
+
+One bench step = one complete solve of the workload (solver state reset to
+x = 0, z = 0, r = y, then every block step of the workload, its residual
+refreshes and epoch averages).  The default workload is the 2D fan-beam scan
+(512^2 pixels, 720 views x 768 curved bins, 8 view blocks x 4 x 4 tiles,
+density-weighted block choice, 200 block steps).
+
+metric: ray-voxel updates/s, where one update applies one non-zero A_ij of the
+block to one vector: every step does one backprojection and two forward
+products, so updates = 3 * nnz(A_{I_g}^J), counted by the kernels.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                        [--workload fan2d_512|cone3d_256|parallel2d_64]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from synth import configs as C  # noqa: E402
+from synth import data as D  # noqa: E402
+
+# Algorithmic FP32 operations per non-zero of A_{I_g}^J, per kernel:
+#   traversal: next plane crossing (subtract, multiply) + choose the nearest (1)  = 3
+#   backprojection: length (1) + length * r (1) + add into the tile (1)            = 3
+#   dual forward: length (1) + two multiply-adds (2 x 2)                          = 5
+ALG_FLOP = {"backproject": 6.0, "forward_dual": 8.0}
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="fan2d_512", choices=sorted(C.ALL))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def oracle_sample(cfg, y, seconds: float, max_steps: int | None = None):
+    """Time the oracle's block steps (Alg. 1 inside Alg. 2-4) for about `seconds`."""
+    from oracle import siddon
+    from oracle.blocks import Partition as OPart, block_nnz
+    from oracle.geometry import Geometry as OGeom
+    from oracle.solver import OracleSolver
+    og = OGeom(**cfg["geom"])
+    op = OPart(og, cfg["part"]["tiles"], cfg["part"]["view_blocks"], cfg["part"]["det_blocks"])
+    o = OracleSolver(op, cfg["solver"], y.astype(np.float64))
+    o._new_epoch()
+    spent, steps, nnz = 0.0, 0, 0
+    while o.queue and (max_steps is None or steps < max_steps):
+        j, grp, _ = o.queue.pop(0)
+        t0 = time.perf_counter()
+        o.step(j, grp)
+        spent += time.perf_counter() - t0
+        nnz += block_nnz(op, grp, j)
+        steps += 1
+        if spent >= seconds:
+            break
+    return dict(seconds=spent, steps=steps, nnz=nnz, cores=siddon.num_threads())
+
+
+def run_reference(args, cfg, world, rank):
+    """--impl reference: the FP64 oracle, on the host cores, on this workload."""
+    if rank != 0:
+        return 0
+    y, _ = D.make_data(cfg)
+    # every step is one oracle block step: W warm-up steps, then K timed ones
+    from oracle.blocks import Partition as OPart, block_nnz
+    from oracle.geometry import Geometry as OGeom
+    from oracle.solver import OracleSolver
+    og = OGeom(**cfg["geom"])
+    op = OPart(og, cfg["part"]["tiles"], cfg["part"]["view_blocks"], cfg["part"]["det_blocks"])
+    o = OracleSolver(op, cfg["solver"], y.astype(np.float64))
+    o._new_epoch()
+    for _ in range(args.warmup):
+        if not o.queue:
+            o._new_epoch()
+        j, grp, _ = o.queue.pop(0)
+        o.step(j, grp)
+    t = 0.0
+    nnz = 0
+    for _ in range(args.steps):
+        if not o.queue:
+            o._new_epoch()
+        j, grp, _ = o.queue.pop(0)
+        t0 = time.perf_counter()
+        o.step(j, grp)
+        t += time.perf_counter() - t0
+        nnz += block_nnz(op, grp, j)
+    from oracle import siddon
+    value = 3.0 * nnz / t
+    line = {
+        "impl": "reference", "metric": "ray-voxel updates/s", "value": value,
+        "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["name"], "step": "one block step (Alg. 1) of the workload"},
+        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": siddon.num_threads(),
+                         "kind": "oracle",
+                         "sample": "%d block steps of %s after %d warm-up steps"
+                                   % (args.steps, cfg["name"], args.warmup)},
+        "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, cfg, world, rank, local):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import __graft_entry__ as GE
+    GE.build()
+    from paper_1709_00953_gb300 import csgd
+
+    big = cfg["geom"]["kind"] == "cone3d"
+    y, _ = D.make_data(cfg, device=str(dev) if big else None)
+    g = csgd.Geometry(cfg["geom"])
+    p = csgd.Partition(g, **cfg["part"])
+    yt = torch.tensor(y, device=dev)
+    stream = torch.cuda.current_stream()
+    solver = csgd.Solver(p, cfg["solver"], yt)
+    steps = cfg["steps"]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def one_solve():
+        solver.reset(yt)
+        solver.solve(steps, None, report=False)
+
+    for _ in range(args.warmup):
+        one_solve()
+    rep = None
+    solver.reset(yt)
+    rep = solver.solve(steps, None, report=True)
+    nnz_per_solve = rep["nnz"]
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident, L2 flushed before every step ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    solver.profile(True)
+    solver.profile_read(reset=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        one_solve()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    ck = clocks.stop()
+    prof = solver.profile_read(reset=True)
+    solver.profile(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        ms = float(t.item())
+    updates = 3.0 * nnz_per_solve * args.steps * world
+    value = updates / (ms / 1e3)
+
+    # ---- end to end through the public API: pinned host y in, host x out ----
+    e2e = None
+    if not args.no_e2e:
+        y_host = torch.tensor(y).pin_memory()
+        x_host = torch.empty(p.n_voxels, dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            solver.reset(y_host)
+            solver.solve(steps, x_host, report=False)
+        torch.cuda.synchronize()
+        e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            e_ev[k][0].record(stream)
+            solver.reset(y_host)
+            solver.solve(steps, x_host, report=False)
+            e_ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        e_ms = sum(a.elapsed_time(b) for a, b in e_ev)
+        if world > 1:
+            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": updates / (e_ms / 1e3), "unit": "updates/s",
+               "h2d_bytes_per_step": int(4 * p.n_rays), "d2h_bytes_per_step": int(4 * p.n_voxels),
+               "ms_per_step": e_ms / args.steps}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel ----
+    kern = {k: v for k, v in prof.items() if v["launches"] > 0}
+    total_ms = sum(v["ms"] for v in kern.values())
+    dom = max(("backproject", "forward_dual"), key=lambda k: kern.get(k, {"ms": 0})["ms"])
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = ck["sm_mhz"] if ck else measured_peaks().get("clocks_under_load", {}).get("sm_mhz_median", 1507.0)
+    peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    flop = ALG_FLOP[dom] * nnz_per_solve * args.steps
+    achieved = flop / (kern[dom]["ms"] / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops,
+            "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+            "peak_basis": "FP32 FMA: %d SMs x %d lanes x 2 x %.0f MHz (median SM clock of this run)"
+                          % (sm_count, FP32_LANES_PER_SM, mhz),
+            "flop_per_nnz": ALG_FLOP[dom]}
+    launches = int(sum(v["launches"] for v in prof.values()))
+    kernels = {k: {"launches": int(v["launches"]), "ms": v["ms"],
+                   "share": (v["ms"] / total_ms if total_ms else 0.0)} for k, v in kern.items()}
+
+    cpu = None
+    if not args.no_cpu:
+        res = oracle_sample(cfg, y, seconds=args.cpu_seconds)
+        cpu = {"value": 3.0 * res["nnz"] / res["seconds"], "unit": "updates/s",
+               "cores": res["cores"], "kind": "oracle",
+               "sample": "first %d block steps of %s (%.1f s of FP64 oracle work)"
+                         % (res["steps"], cfg["name"], res["seconds"])}
+
+    line = {
+        "metric": "ray-voxel updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "block_steps_per_solve": steps,
+                   "nnz_per_solve": int(nnz_per_solve), "n_rays": int(p.n_rays),
+                   "n_voxels": int(p.n_voxels), "l2": "flushed (256 MB write) before each step",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "solves_per_s": 1e3 * args.steps * world / ms},
+        "roofline": roof, "kernels": kernels, "gpu_launches": launches,
+        "wall_s_timed": t_wall,
+    }
+    if ck:
+        line["clocks"] = ck
+    if e2e:
+        line["e2e"] = e2e
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    cfg = C.ALL[args.workload]()
+    if args.impl == "reference":
+        return run_reference(args, cfg, world, rank)
+    return run_gpu(args, cfg, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,271 @@
+/*
+ * csgd.h - C ABI of the GB300 (sm_103a) block solver for y = Ax + e.
+ *
+ * Method: Gao & Blumensath, "Distributed computation of linear inverse problems
+ * with application to computed tomography reconstruction" (arXiv:1709.00953):
+ * coordinate-reduced steepest gradient descent (CSGD, Alg. 1-3) and its grouped
+ * variant (GCSGD, Alg. 4).  A is never stored: every entry A_i^j (length of
+ * ray i inside voxel j, Sec. II-A) is recomputed on the GPU by Siddon traversal.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Status: every function returns an int32_t status, CSGD_OK (0) or a negative
+ *   CSGD_ERR_* code; csgd_last_error() returns a message for the calling
+ *   thread's last failure.  Nothing throws across this ABI.
+ * Handles: created by *_create / csgd_block_partition, released by *_destroy.
+ *   Destroy functions accept NULL and return CSGD_OK.  A partition keeps a
+ *   reference to nothing the caller owns (it copies what it needs), but it must
+ *   outlive the solvers created from it, and a geometry must outlive its
+ *   partitions.
+ * Vectors: FP32, contiguous, owned by the caller, never retained after the
+ *   call returns.  Unless a flag says otherwise they are DEVICE pointers (for
+ *   example torch.Tensor.data_ptr() of a CUDA tensor) on the current device.
+ *   Volumes are row-major [nz][ny][nx] (x fastest; nz = 1 in 2D); sinograms are
+ *   [view][v-bin][u-bin] (u fastest).
+ * Streams: a csgd_stream is a cudaStream_t; NULL is the legacy default stream.
+ *   Device work is enqueued asynchronously on it unless a function says it
+ *   synchronises.  Calls that use the same solver must be issued on one stream
+ *   (or be serialised by the caller).
+ * Geometry (the paper is silent on these; every part of this project uses
+ *   them): the grid is centred on the origin with cubic voxels of edge h; view
+ *   angle t gives the central direction d_c = (-cos t, -sin t, 0), the detector
+ *   axes e_u = (-sin t, cos t, 0) and e_v = (0, 0, 1); the centre of bin k of n
+ *   lies at (k - (n-1)/2) * pitch; flat detectors are perpendicular to d_c at
+ *   distance sdd from the source S = sod (cos t, sin t, 0) (Sec. II-D); the
+ *   curved detector is an arc centred on the source with angular pitch.
+ */
+#ifndef CSGD_H
+#define CSGD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CSGD_OK 0
+#define CSGD_ERR_INVALID_ARG (-1)
+#define CSGD_ERR_OOM (-2)
+#define CSGD_ERR_CUDA (-3)
+#define CSGD_ERR_TIMEOUT (-4)
+#define CSGD_ERR_STATE (-5)
+#define CSGD_ERR_UNSUPPORTED (-6)
+
+typedef struct csgd_geometry csgd_geometry;
+typedef struct csgd_partition csgd_partition;
+typedef struct csgd_solver csgd_solver;
+typedef void* csgd_stream; /* cudaStream_t */
+
+/* ---------------------------------------------------------------------------
+ * Geometry (Sec. II-A model, Sec. II-D / Sec. III scan set-ups)
+ * ------------------------------------------------------------------------- */
+enum {
+    CSGD_PARALLEL_2D = 0,  /* rays along d_c through s_k e_u                   */
+    CSGD_FAN_2D_FLAT = 1,  /* point source, flat detector                      */
+    CSGD_FAN_2D_CURVED = 2,/* point source, detector arc centred on the source */
+    CSGD_CONE_3D = 3,      /* point source on a circle, flat 2D detector       */
+    CSGD_CUSTOM_3D = 4     /* arbitrary per-view source / detector poses       */
+};
+
+typedef struct {
+    int32_t kind;          /* CSGD_PARALLEL_2D .. CSGD_CUSTOM_3D                  */
+    int32_t n[3];          /* voxels along x, y, z (n[2] is ignored in 2D)        */
+    double h;              /* voxel edge (world units, > 0)                       */
+    int32_t n_views;       /* number of views (> 0)                               */
+    const double* angles;  /* host, n_views angles in radians (kinds 0..3)        */
+    const double* poses;   /* host, n_views x 12: S, C, e_u, e_v (CUSTOM_3D only);
+                              e_u, e_v unit, orthogonal, perpendicular to C - S    */
+    int32_t nu, nv;        /* detector bins along e_u and e_v (nv = 1 in 2D)      */
+    double pu, pv;         /* bin pitch (world units; radians along the arc for
+                              CSGD_FAN_2D_CURVED)                                 */
+    double sod, sdd;       /* source-origin and source-detector distance (fan and
+                              cone kinds); the source must lie outside the grid's
+                              circumscribed sphere                                 */
+} csgd_geometry_desc;
+
+/* Validates and copies desc (host arrays are copied).  Host only, no GPU work.
+ * CSGD_ERR_INVALID_ARG on a malformed description. */
+int32_t csgd_geometry_create(const csgd_geometry_desc* desc, csgd_geometry** out);
+int32_t csgd_geometry_destroy(csgd_geometry* geom);
+
+/* ---------------------------------------------------------------------------
+ * Block partition (Eq. e1; Sec. II-D domain decomposition; Alg. 3 P(I,J))
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t tiles[3];      /* column blocks: cuboid tiles per axis; along an axis
+                              with N voxels and T tiles, tile t covers
+                              [floor(tN/T), floor((t+1)N/T)).  Tile index
+                              j = (tz*TY + ty)*TX + tx.  tiles[2] ignored in 2D.  */
+    int32_t view_blocks;   /* number of view sets (ignored if view_block_of)      */
+    const int32_t* view_block_of; /* optional host map view -> view set (values
+                              0..B-1, every set non-empty); NULL = contiguous
+                              views split at floor(kV/B)                           */
+    int32_t det_blocks_u;  /* detector sub-areas along u (bins split at floor(k nu/DU)) */
+    int32_t det_blocks_v;  /* ... and along v                                     */
+} csgd_partition_desc;
+
+typedef struct {
+    int32_t m;             /* row blocks: m = B * DV * DU; row block
+                              i = (vb*DV + dv)*DU + du = view set x sub-area      */
+    int32_t n;             /* column blocks (tiles)                               */
+    int64_t n_rays;        /* rows of A = n_views * nu * nv                        */
+    int64_t n_voxels;      /* columns of A                                        */
+    int64_t z_floats;      /* floats of the solver's z store (shadow rectangles)  */
+} csgd_partition_info;
+
+/* Builds the row and column blocks, the importance table P(I,J) = P_S/P_T of
+ * Alg. 3 (exact shadow of each tile, in detector-bin units) and the per
+ * (view, tile) ray tables, and uploads the tables to the current device
+ * (synchronously).  CSGD_ERR_INVALID_ARG on bad counts, CSGD_ERR_OOM /
+ * CSGD_ERR_CUDA on device failures. */
+int32_t csgd_block_partition(const csgd_geometry* geom, const csgd_partition_desc* desc,
+                             csgd_partition** out);
+int32_t csgd_partition_destroy(csgd_partition* part);
+int32_t csgd_partition_get_info(const csgd_partition* part, csgd_partition_info* info);
+
+/* P(I,J) of Alg. 3 as an m x n row-major host array P[i*n + j] (FP64). */
+int32_t csgd_partition_probabilities(const csgd_partition* part, double* P);
+
+/* ---------------------------------------------------------------------------
+ * Block operators (Alg. 1: z_I = A_I^J x_J and g_J = (A_I^J)^T r_I)
+ * ------------------------------------------------------------------------- */
+/* out[i] = (accumulate ? out[i] : 0) + sum_{j in J} A_ij x_j for every row i of
+ * the union of the row blocks row_blocks[0..n_rb) (host array, distinct
+ * indices); column block J = tile j.  x: full volume (device); out: full
+ * sinogram (device); rows outside the union are not touched.  Lengths are
+ * recomputed by Siddon traversal in FP32 with compensated accumulation. */
+int32_t csgd_project_block(const csgd_partition* part, const int32_t* row_blocks, int32_t n_rb,
+                           int32_t j, const float* x, float* out, int32_t accumulate,
+                           csgd_stream stream);
+
+/* g[v] = (accumulate ? g[v] : 0) + sum_{i in I} A_iv r_i for every voxel v of
+ * tile j (other voxels untouched); I = union of row_blocks.  r: full sinogram
+ * (device); g: full volume (device).  The same Siddon lengths as
+ * csgd_project_block, accumulated per tile in shared memory (no global
+ * atomics) and reduced across a thread-block cluster. */
+int32_t csgd_backproject_block(const csgd_partition* part, const int32_t* row_blocks,
+                               int32_t n_rb, int32_t j, const float* r, float* g,
+                               int32_t accumulate, csgd_stream stream);
+
+/* out = A x over all rows and all tiles (device pointers). */
+int32_t csgd_project_full(const csgd_partition* part, const float* x, float* out,
+                          csgd_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Solver (Alg. 2 / 3 / 4 around the Alg. 1 step)
+ * ------------------------------------------------------------------------- */
+enum { CSGD_SAMPLE_SEQUENTIAL = 0, CSGD_SAMPLE_UNIFORM = 1, CSGD_SAMPLE_IMPORTANCE = 2,
+       CSGD_SAMPLE_MIXED = 3 };
+enum { CSGD_SYNC_COLUMN = 0, CSGD_SYNC_EPOCH = 1 };
+
+typedef struct {
+    int32_t sampling;      /* CSGD_SAMPLE_*: Alg. 2 order, uniform, Alg. 3
+                              importance, Sec. III-E mixed                        */
+    int32_t sync;          /* CSGD_SYNC_COLUMN: refresh r after each column block
+                              (Alg. 2-4 as printed); CSGD_SYNC_EPOCH: one refresh
+                              per epoch (Sec. II-F parameter-server reading)       */
+    int32_t group_size;    /* s of Alg. 4 (1 = CSGD)                               */
+    int32_t reserved;
+    double alpha;          /* fraction of row blocks drawn per column block       */
+    double gamma;          /* fraction of column blocks visited per epoch         */
+    double b;              /* beta = b * P_S(I_g,J) / P_T(J)                       */
+    double theta_step;     /* mixed sampling: theta grows by this per epoch       */
+    uint64_t seed;         /* SplitMix64 seed of the block schedule               */
+} csgd_solver_params;
+
+/* Random choice of blocks, shared bit-for-bit with any implementation of the
+ * same rules: SplitMix64 (Steele, Lea & Flood 2014); per epoch a Fisher-Yates
+ * column permutation (first ceil(gamma n) columns), then per column
+ * ceil(alpha m / s) groups of s weighted draws without replacement (walk the
+ * remaining blocks in index order; the first whose running weight sum exceeds
+ * u * total is taken; drawing stops when no positive weight is left).
+ * Writes, for n_epochs epochs from the seed, the flat encoding
+ *   per epoch: n_cols, then per column: j, n_groups, then per group: size, rows...
+ * into out (host, capacity ints); *len receives the length (also when the
+ * capacity is too small, in which case CSGD_ERR_INVALID_ARG is returned). */
+int32_t csgd_schedule_generate(const csgd_partition* part, const csgd_solver_params* params,
+                               int32_t n_epochs, int32_t* out, int64_t capacity, int64_t* len);
+
+/* Device bytes a solver on this partition allocates (admission control). */
+int32_t csgd_solver_footprint_bytes(const csgd_partition* part, const csgd_solver_params* params,
+                                    int64_t* bytes);
+
+/* Allocates the solver state on the current device and initialises it from y
+ * (device sinogram, copied): x = 0, z = 0, r = y (Alg. 2 initialisation).
+ * Synchronises the stream.  CSGD_ERR_OOM when the device is full. */
+int32_t csgd_solver_create(const csgd_partition* part, const csgd_solver_params* params,
+                           const float* y, csgd_stream stream, csgd_solver** out);
+int32_t csgd_solver_destroy(csgd_solver* solver);
+
+/* Re-initialises the state from new data y (host pointer if y_on_host != 0,
+ * else device) and restarts the schedule from the seed.  Asynchronous. */
+int32_t csgd_solver_reset(csgd_solver* solver, const float* y, int32_t y_on_host,
+                          csgd_stream stream);
+
+typedef struct {
+    int32_t j;             /* column block                                        */
+    int32_t n_rows;        /* number of row blocks in the group                   */
+    const int32_t* row_blocks; /* host, distinct row block indices                */
+} csgd_block_choice;
+
+typedef struct {
+    int64_t step;          /* global step index                                   */
+    int32_t j;             /* column block (-1 in csgd_solver_history)            */
+    int32_t n_rows;        /* row blocks in the group (-1 in csgd_solver_history) */
+    double beta, gg, qq, mu; /* beta of Alg. 3; g^T g; ||A g||^2; step length      */
+    int64_t nnz;           /* non-zeros of A_{I_g}^J (history only)               */
+} csgd_step_info;
+
+/* One Alg. 1 step.  choice == NULL takes the next step of the schedule (and
+ * ends the column batch / epoch when the schedule does); otherwise the given
+ * block choice is applied as a batch of its own (refresh after it).  If info is
+ * non-NULL the stream is synchronised and the step's scalars are returned. */
+int32_t csgd_solve_step(csgd_solver* solver, const csgd_block_choice* choice,
+                        csgd_step_info* info, csgd_stream stream);
+
+typedef struct {
+    int64_t steps;         /* steps executed by this call                         */
+    int64_t epochs;        /* epochs closed so far                                */
+    int64_t nnz;           /* non-zeros of A visited by the forward passes        */
+    double updates;        /* ray-voxel updates = 3 * nnz (one backprojection and
+                              two forward products per non-zero)                  */
+    double residual_norm;  /* ||y - A x|| (FP64), only if compute_residual       */
+} csgd_report;
+
+/* Runs n_steps steps of the schedule, then closes the epoch (refresh and
+ * averaging, even mid-epoch) and writes x (row-major volume) to x_out (host
+ * pointer if x_on_host != 0, else device; may be NULL).  If report is non-NULL
+ * the stream is synchronised and the report filled; compute_residual != 0 adds
+ * a full forward projection for ||y - A x||. */
+int32_t csgd_solve(csgd_solver* solver, int64_t n_steps, float* x_out, int32_t x_on_host,
+                   csgd_report* report, int32_t compute_residual, csgd_stream stream);
+
+/* Copies the per-step scalars of the last `capacity` steps since the last reset
+ * (oldest first) to out (host); *count receives how many were written. */
+int32_t csgd_solver_history(csgd_solver* solver, csgd_step_info* out, int64_t capacity,
+                            int64_t* count);
+
+/* Per-kernel timing (the paper has no counterpart; it supports the roofline
+ * measurements).  While enabled, every kernel launch of csgd_solve /
+ * csgd_solve_step is bracketed by CUDA events on the caller's stream.
+ * csgd_solver_profile_read synchronises on the last event and sums the
+ * elapsed times per kernel kind: 0 backprojection, 1 dual forward product,
+ * 2 epilogue (z, r, x^ updates), 3 epoch close (averaging). */
+typedef struct {
+    int64_t launches[4];
+    double ms[4];
+} csgd_kernel_times;
+int32_t csgd_solver_profile(csgd_solver* solver, int32_t enable);
+int32_t csgd_solver_profile_read(csgd_solver* solver, csgd_kernel_times* out, int32_t reset);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* csgd_last_error(void);
+
+/* Library version string. */
+const char* csgd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSGD_H */

@@ -162,3 +162,12 @@ def block_matrix(part: Partition, row_blocks, j: int):
     org, d = g.rays(rows)
     A = siddon.system_matrix(g.grid, org, d)
     return A[:, part.tile_voxels(j)]
+
+
+def block_nnz(part: Partition, row_blocks, j: int) -> int:
+    """Number of non-zeros of A_I^J (I = union of row_blocks, J = tile j)."""
+    g = part.geom
+    rows = part.rows_of(row_blocks)
+    org, d = g.rays(rows)
+    lo, hi = part.tile_box(j)
+    return siddon.count_box(g.grid, org, d, lo, hi)

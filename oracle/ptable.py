@@ -13,7 +13,10 @@ area of J on the whole detector over the whole trajectory.  The readings used:
 * a row block I with several views sums the per-view overlaps, so a group
   I_g = union of row blocks has P_S(I_g, J) = sum of the members' P_S and
   beta = b * P_S(I_g, J) / P_T(J) grows with the group, as Sec. III-C notes;
-* P_T(J) = 0 (a tile no ray sees) gives P(., J) = 0.
+* P_T(J) = 0 (a tile no ray sees) gives P(., J) = 0;
+* an overlap below 1e-9 bin units counts as none: a shadow edge that falls
+  exactly on a sub-area boundary otherwise leaves a rounding sliver whose sign
+  decides whether the block can be drawn at all.
 
 Pinned in ``tests/test_oracle_ptable.py`` by the parallel-beam closed form of
 the shadow width, sum_I P(I, J) = 1, symmetry and hand-computed hull cases.
@@ -23,6 +26,8 @@ from __future__ import annotations
 import numpy as np
 
 from .blocks import Partition
+
+SLIVER = 1e-9  # overlaps below this many bin units count as zero
 
 
 def _tile_corners(part: Partition, j: int) -> np.ndarray:
@@ -110,8 +115,10 @@ def overlap(part: Partition, v: int, j: int, u0, u1, v0, v1) -> float:
     s = shadow(part, v, j)
     if part.geom.dim == 2:
         lo, hi = s
-        return max(0.0, min(hi, u1) - max(lo, u0))
-    return polygon_area(clip_polygon_rect(s, u0, u1, v0, v1))
+        a = max(0.0, min(hi, u1) - max(lo, u0))
+    else:
+        a = polygon_area(clip_polygon_rect(s, u0, u1, v0, v1))
+    return a if a > SLIVER else 0.0
 
 
 def shadow_tables(part: Partition):

@@ -27,7 +27,8 @@
  *   oracle_siddon_count  - number of non-zeros of each ray (row of A);
  *   oracle_siddon_fill   - CSR column indices and lengths of those rows;
  *   oracle_project_box   - out_i = sum_{j in box} A_ij x_j       (A_I^J x_J);
- *   oracle_backproject_box - g_j += sum_i A_ij r_i for j in box ((A_I^J)^T r_I).
+ *   oracle_backproject_box - g_j += sum_i A_ij r_i for j in box ((A_I^J)^T r_I);
+ *   oracle_count_box     - number of non-zeros of A_I^J (rays x box).
  * A "box" is an index range [blo, bhi) per axis; it selects the column block J.
  */
 #include <math.h>
@@ -229,6 +230,30 @@ void oracle_project_box(int dim, const int64_t* n, double h, const double* lo,
         free(cols);
         free(lens);
     }
+}
+
+int64_t oracle_count_box(int dim, const int64_t* n, double h, const double* lo,
+                         int64_t n_rays, const double* org, const double* dir,
+                         const int64_t* blo, const int64_t* bhi) {
+    grid_t g;
+    make_grid(&g, dim, n, h, lo);
+    int64_t cap = max_entries(&g);
+    int64_t total = 0;
+#pragma omp parallel reduction(+ : total)
+    {
+        double* alpha = (double*)malloc(sizeof(double) * (size_t)cap);
+        int64_t* cols = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+        double* lens = (double*)malloc(sizeof(double) * (size_t)cap);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < n_rays; ++i) {
+            int64_t c = ray_entries(&g, org + 3 * i, dir + 3 * i, alpha, cols, lens);
+            for (int64_t k = 0; k < c; ++k) total += in_box(&g, cols[k], blo, bhi);
+        }
+        free(alpha);
+        free(cols);
+        free(lens);
+    }
+    return total;
 }
 
 void oracle_backproject_box(int dim, const int64_t* n, double h, const double* lo,

@@ -53,6 +53,8 @@ def _load():
             lib.oracle_project_box.restype = None
             lib.oracle_backproject_box.argtypes = common + [i64p, i64p, f64p, f64p]
             lib.oracle_backproject_box.restype = None
+            lib.oracle_count_box.argtypes = common + [i64p, i64p]
+            lib.oracle_count_box.restype = ctypes.c_int64
             lib.oracle_num_threads.restype = ctypes.c_int
             lib.oracle_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -146,3 +148,18 @@ def backproject_box(grid, org, dirs, box_lo, box_hi, r) -> np.ndarray:
     lib.oracle_backproject_box(dim, _p(n, i64), h, _p(lo, f64), org.shape[0], _p(org, f64),
                                _p(dirs, f64), _p(blo, i64), _p(bhi, i64), _p(r, f64), _p(g, f64))
     return g
+
+
+def count_box(grid, org, dirs, box_lo, box_hi) -> int:
+    """Number of non-zeros A_ij with voxel j inside the index box."""
+    lib = _load()
+    dim, n, h, lo = _grid_args(grid)
+    org, dirs = _rays(org, dirs)
+    blo = np.zeros(3, np.int64)
+    bhi = np.ones(3, np.int64)
+    blo[:dim] = box_lo
+    bhi[:dim] = box_hi
+    i64 = ctypes.c_int64
+    f64 = ctypes.c_double
+    return int(lib.oracle_count_box(dim, _p(n, i64), h, _p(lo, f64), org.shape[0], _p(org, f64),
+                                    _p(dirs, f64), _p(blo, i64), _p(bhi, i64)))

@@ -1,0 +1,939 @@
+// The C ABI of include/csgd.h: handles, argument checks, device tables and the
+// solver's host-side schedule (Alg. 2 / 3 / 4 around the Alg. 1 step).
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/csgd.h"
+#include "host.h"
+#include "ops.h"
+
+using namespace csgd;
+
+struct csgd_geometry {
+    Geometry g;
+};
+
+struct csgd_partition {
+    Partition p;
+    std::mutex mu;
+    bool on_device = false;
+    int sm_count = 0;
+    int64_t max_rays_per_block_tile = 0;  // max over (i, j) of rays of row block i in tile j
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(e == cudaErrorMemoryAllocation ? CSGD_ERR_OOM : CSGD_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CSGD_CUDA(call, where)                       \
+    do {                                             \
+        cudaError_t _e = (call);                     \
+        if (_e != cudaSuccess) return cuda_fail(_e, where); \
+    } while (0)
+
+// Upload the partition's tables to the current device on first use.
+int ensure_device(csgd_partition* P) {
+    std::lock_guard<std::mutex> lk(P->mu);
+    int dev = 0;
+    CSGD_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (P->on_device) {
+        if (dev != P->p.device)
+            return fail(CSGD_ERR_INVALID_ARG, "partition tables live on another device");
+        return CSGD_OK;
+    }
+    Partition& p = P->p;
+    p.device = dev;
+    CSGD_CUDA(cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, dev),
+              "cudaDeviceGetAttribute");
+    size_t bv = sizeof(DevView) * p.views_h.size();
+    size_t bt = sizeof(DevVT) * p.vt_h.size();
+    size_t bti = sizeof(DevTile) * p.tiles_h.size();
+    CSGD_CUDA(cudaMalloc(&p.d_views, bv), "cudaMalloc(views)");
+    CSGD_CUDA(cudaMalloc(&p.d_vt, bt), "cudaMalloc(view-tile table)");
+    CSGD_CUDA(cudaMalloc(&p.d_tiles, bti), "cudaMalloc(tiles)");
+    CSGD_CUDA(cudaMemcpy(p.d_views, p.views_h.data(), bv, cudaMemcpyHostToDevice), "upload views");
+    CSGD_CUDA(cudaMemcpy(p.d_vt, p.vt_h.data(), bt, cudaMemcpyHostToDevice), "upload table");
+    CSGD_CUDA(cudaMemcpy(p.d_tiles, p.tiles_h.data(), bti, cudaMemcpyHostToDevice),
+              "upload tiles");
+    p.dg.views = p.d_views;
+    p.dg.vt = p.d_vt;
+    p.dg.tiles = p.d_tiles;
+    P->on_device = true;
+    return CSGD_OK;
+}
+
+int check_rows(const Partition& p, const int32_t* rows, int32_t n_rb) {
+    if (n_rb < 1 || !rows) return fail(CSGD_ERR_INVALID_ARG, "need at least one row block");
+    std::vector<char> seen(p.m, 0);
+    for (int k = 0; k < n_rb; ++k) {
+        if (rows[k] < 0 || rows[k] >= p.m) return fail(CSGD_ERR_INVALID_ARG, "row block out of range");
+        if (seen[rows[k]]) return fail(CSGD_ERR_INVALID_ARG, "row blocks must be distinct");
+        seen[rows[k]] = 1;
+    }
+    return CSGD_OK;
+}
+
+// Items of the stand-alone operators: every view of every row block, over the
+// whole sub-rectangle (rays that miss the tile produce exact zeros) when
+// `full_subrect`, else clipped to the tile's shadow rectangle.
+void items_for_rows(const Partition& p, const int32_t* rows, int n_rb, int j, bool full_subrect,
+                    std::vector<WorkItem>* out) {
+    for (int r = 0; r < n_rb; ++r) {
+        int su0, su1, sv0, sv1;
+        p.subrect(rows[r], &su0, &su1, &sv0, &sv1);
+        for (int v : p.views_of(rows[r])) {
+            WorkItem w;
+            w.view = v;
+            w.slot = 0;
+            if (full_subrect) {
+                w.u0 = su0; w.u1 = su1; w.v0 = sv0; w.v1 = sv1;
+            } else {
+                const DevVT& e = p.vt(v, j);
+                w.u0 = std::max(su0, e.u0); w.u1 = std::min(su1, e.u1);
+                w.v0 = std::max(sv0, e.v0); w.v1 = std::min(sv1, e.v1);
+                if (w.u1 <= w.u0 || w.v1 <= w.v0) continue;
+            }
+            w.ray_off = 0;
+            out->push_back(w);
+        }
+    }
+}
+
+// Launch the stand-alone forward / backward operator over `items` in chunks
+// that fit the kernel parameter space.
+int run_inline(csgd_partition* P, const std::vector<WorkItem>& items, int j, bool forward,
+               const float* in, float* out, int accumulate, cudaStream_t s) {
+    const Partition& p = P->p;
+    InlineItems* it = new (std::nothrow) InlineItems;
+    if (!it) return fail(CSGD_ERR_OOM, "host allocation");
+    size_t pos = 0;
+    bool first = true;
+    int rc = CSGD_OK;
+    while (pos < items.size() || first) {
+        size_t cnt = std::min(items.size() - pos, (size_t)kMaxInlineItems);
+        memset(&it->step, 0, sizeof(it->step));
+        it->step.j = j;
+        it->step.w0 = 0;
+        it->step.w1 = (int32_t)cnt;
+        it->n = (int32_t)cnt;
+        int64_t rays = 0;
+        for (size_t k = 0; k < cnt; ++k) {
+            it->items[k] = items[pos + k];
+            it->items[k].ray_off = rays;
+            rays += (int64_t)(it->items[k].u1 - it->items[k].u0) * (it->items[k].v1 - it->items[k].v0);
+        }
+        it->step.n_rays = rays;
+        int acc = (first ? accumulate : 1);
+        cudaError_t e;
+        if (forward) {
+            e = launch_project_inline(p.dg, *it, in, out, accumulate, s);
+        } else if (cnt == 0) {
+            // no rays: g = 0 on the tile unless accumulating
+            if (!acc) {
+                InlineItems empty;
+                memset(&empty.step, 0, sizeof(empty.step));
+                empty.step.j = j;
+                empty.n = 0;
+                e = launch_backproject_inline(p.dg, p.tiles_h[j], empty, in, out, 0, P->sm_count, s);
+            } else {
+                e = cudaSuccess;
+            }
+        } else {
+            e = launch_backproject_inline(p.dg, p.tiles_h[j], *it, in, out, acc, P->sm_count, s);
+        }
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, forward ? "project kernel" : "backproject kernel");
+            break;
+        }
+        pos += cnt;
+        first = false;
+        if (cnt == 0) break;
+    }
+    delete it;
+    return rc;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Solver
+// ===========================================================================
+struct QueuedStep {
+    int j;
+    std::vector<int> group;
+    bool last_in_batch;
+};
+
+struct csgd_solver {
+    csgd_partition* P = nullptr;
+    csgd_solver_params prm{};
+    SolverBuffers sb{};
+    int64_t n_rays = 0, n_vox = 0;
+    SplitMix64 rng{0};
+    int64_t epoch = 0;       // epochs closed
+    int64_t steps_done = 0;  // since the last reset
+    std::deque<QueuedStep> queue;  // rest of the current epoch
+    bool epoch_open = false;        // candidates accumulated since the last close
+    int max_slots = 1;
+    int last_group = 0;             // row blocks of the last planned step
+    int64_t max_rays_per_step = 0;
+    // device arrays for the schedule of one solve call
+    WorkItem* d_items = nullptr;
+    int64_t items_cap = 0;
+    StepDesc* d_steps = nullptr;
+    int64_t steps_cap = 0;
+    // temporaries for the residual norm
+    float* d_xrow = nullptr;
+    float* d_ax = nullptr;
+    double* d_sq = nullptr;
+    int64_t bytes = 0;
+    std::vector<void*> allocs;
+    // optional per-kernel timing with CUDA events
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec {
+        int kind;
+        int e0, e1;
+    };
+    std::vector<Rec> recs;
+    size_t ev_used = 0;
+};
+
+namespace {
+
+int dmalloc(csgd_solver* S, void** ptr, size_t bytes, const char* what) {
+    cudaError_t e = cudaMalloc(ptr, bytes == 0 ? 16 : bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return cuda_fail(e, what);
+    }
+    S->allocs.push_back(*ptr);
+    S->bytes += (int64_t)bytes;
+    return CSGD_OK;
+}
+
+void dfree(csgd_solver* S, void* ptr) {
+    if (!ptr) return;
+    auto it = std::find(S->allocs.begin(), S->allocs.end(), ptr);
+    if (it != S->allocs.end()) S->allocs.erase(it);
+    cudaFree(ptr);
+}
+
+int64_t max_rays_per_step(const Partition& p, int s) {
+    // largest sum over one row block's views of its clipped shadow rectangles,
+    // times the group size
+    int64_t best = 0;
+    for (int i = 0; i < p.m; ++i) {
+        int su0, su1, sv0, sv1;
+        p.subrect(i, &su0, &su1, &sv0, &sv1);
+        for (int j = 0; j < p.n; ++j) {
+            int64_t rays = 0;
+            for (int v : p.views_of(i)) {
+                const DevVT& e = p.vt(v, j);
+                int u0 = std::max(su0, e.u0), u1 = std::min(su1, e.u1);
+                int v0 = std::max(sv0, e.v0), v1 = std::min(sv1, e.v1);
+                if (u1 > u0 && v1 > v0) rays += (int64_t)(u1 - u0) * (v1 - v0);
+            }
+            best = std::max(best, rays);
+        }
+    }
+    return best * s;
+}
+
+int groups_per_column(const Partition& p, const csgd_solver_params& prm) {
+    int s = std::max(1, prm.group_size);
+    double v = ceil(prm.alpha * p.m / s - 1e-9);
+    return std::max(1, std::min((int)v, p.m));
+}
+
+int validate_params(const Partition& p, const csgd_solver_params* prm) {
+    if (!prm) return fail(CSGD_ERR_INVALID_ARG, "params is NULL");
+    if (prm->sampling < 0 || prm->sampling > 3) return fail(CSGD_ERR_INVALID_ARG, "bad sampling");
+    if (prm->sync < 0 || prm->sync > 1) return fail(CSGD_ERR_INVALID_ARG, "bad sync");
+    if (prm->group_size < 1 || prm->group_size > p.m)
+        return fail(CSGD_ERR_INVALID_ARG, "group size must be in [1, m]");
+    if (!(prm->alpha > 0) || prm->alpha > 1.0 + 1e-12)
+        return fail(CSGD_ERR_INVALID_ARG, "alpha must be in (0, 1]");
+    if (!(prm->gamma > 0) || prm->gamma > 1.0 + 1e-12)
+        return fail(CSGD_ERR_INVALID_ARG, "gamma must be in (0, 1]");
+    if (!(prm->b >= 0) || !std::isfinite(prm->b)) return fail(CSGD_ERR_INVALID_ARG, "bad b");
+    if (!(prm->theta_step >= 0)) return fail(CSGD_ERR_INVALID_ARG, "bad theta_step");
+    return CSGD_OK;
+}
+
+int64_t bp_partials_per_slot(const csgd_partition* P) {
+    const Partition& p = P->p;
+    int64_t best = 1;
+    for (int j = 0; j < p.n; ++j) {
+        BPPlan pl = plan_backprojection(p.dg, p.tiles_h[j], 1, std::max(1, P->sm_count));
+        best = std::max<int64_t>(best, (int64_t)pl.nsb * pl.C);
+    }
+    return best;
+}
+
+int solver_reset_state(csgd_solver* S, cudaStream_t s) {
+    const SolverBuffers& b = S->sb;
+    CSGD_CUDA(cudaMemcpyAsync(b.r, b.y, sizeof(float) * S->n_rays, cudaMemcpyDeviceToDevice, s),
+              "r = y");
+    CSGD_CUDA(cudaMemsetAsync(b.x, 0, sizeof(float) * S->n_vox, s), "x = 0");
+    CSGD_CUDA(cudaMemsetAsync(b.xh, 0, sizeof(float) * S->n_vox, s), "xhat = 0");
+    CSGD_CUDA(cudaMemsetAsync(b.cnt, 0, sizeof(int32_t) * S->P->p.n, s), "count = 0");
+    CSGD_CUDA(cudaMemsetAsync(b.z, 0, sizeof(float) * std::max<int64_t>(1, S->P->p.z_floats), s),
+              "z = 0");
+    if (b.d) CSGD_CUDA(cudaMemsetAsync(b.d, 0, sizeof(float) * S->n_rays, s), "d = 0");
+    CSGD_CUDA(cudaMemsetAsync(b.nnz, 0, sizeof(unsigned long long), s), "nnz = 0");
+    CSGD_CUDA(cudaMemsetAsync(b.counters, 0, sizeof(unsigned) * b.max_slots, s), "counters");
+    CSGD_CUDA(cudaMemsetAsync(b.nnz_slot, 0, sizeof(unsigned long long) * b.max_slots, s),
+              "slot counters");
+    S->rng = SplitMix64(S->prm.seed);
+    S->epoch = 0;
+    S->steps_done = 0;
+    S->queue.clear();
+    S->epoch_open = false;
+    return CSGD_OK;
+}
+
+int ensure_history(csgd_solver* S, int64_t need, cudaStream_t s) {
+    if (need <= S->sb.hist_cap) return CSGD_OK;
+    int64_t cap = std::max<int64_t>(need, 2 * S->sb.hist_cap);
+    double* nh = nullptr;
+    int rc = dmalloc(S, (void**)&nh, sizeof(double) * kHistCols * cap, "cudaMalloc(history)");
+    if (rc) return rc;
+    if (S->sb.hist && S->sb.hist_cap > 0)
+        CSGD_CUDA(cudaMemcpyAsync(nh, S->sb.hist, sizeof(double) * kHistCols * S->sb.hist_cap,
+                                  cudaMemcpyDeviceToDevice, s), "history copy");
+    CSGD_CUDA(cudaStreamSynchronize(s), "history sync");
+    dfree(S, S->sb.hist);
+    S->sb.hist = nh;
+    S->sb.hist_cap = cap;
+    return CSGD_OK;
+}
+
+int ensure_sched_capacity(csgd_solver* S, int64_t n_items, int64_t n_steps, cudaStream_t s) {
+    if (n_items > S->items_cap || n_steps > S->steps_cap) {
+        CSGD_CUDA(cudaStreamSynchronize(s), "schedule buffer sync");
+    }
+    if (n_items > S->items_cap) {
+        dfree(S, S->d_items);
+        S->d_items = nullptr;
+        int64_t cap = std::max<int64_t>(n_items, 2 * S->items_cap);
+        int rc = dmalloc(S, (void**)&S->d_items, sizeof(WorkItem) * cap, "cudaMalloc(items)");
+        if (rc) return rc;
+        S->items_cap = cap;
+    }
+    if (n_steps > S->steps_cap) {
+        dfree(S, S->d_steps);
+        S->d_steps = nullptr;
+        int64_t cap = std::max<int64_t>(n_steps, 2 * S->steps_cap);
+        int rc = dmalloc(S, (void**)&S->d_steps, sizeof(StepDesc) * cap, "cudaMalloc(steps)");
+        if (rc) return rc;
+        S->steps_cap = cap;
+    }
+    return CSGD_OK;
+}
+
+void fill_queue(csgd_solver* S) {
+    const Partition& p = S->P->p;
+    std::vector<ColumnBatch> ep = epoch_schedule(S->rng, p, S->prm, S->epoch);
+    for (auto& cb : ep)
+        for (size_t g = 0; g < cb.groups.size(); ++g)
+            S->queue.push_back(QueuedStep{cb.j, cb.groups[g], g + 1 == cb.groups.size()});
+}
+
+struct Plan {
+    std::vector<WorkItem> items;
+    std::vector<StepDesc> steps;
+    // sequence: batch (first, n) or epoch close (n == -1)
+    struct Op {
+        int first, n, j;
+        int64_t max_rays;
+    };
+    std::vector<Op> ops;
+};
+
+double beta_of(const csgd_solver* S, int j, const std::vector<int>& group) {
+    const Partition& p = S->P->p;
+    double s = 0.0;
+    for (int i : group) s += p.P[(size_t)i * p.n + j];
+    return S->prm.b * s;
+}
+
+void plan_step(csgd_solver* S, Plan* pl, int j, const std::vector<int>& group, int slot) {
+    const Partition& p = S->P->p;
+    StepDesc sd;
+    memset(&sd, 0, sizeof(sd));
+    sd.j = j;
+    sd.w0 = (int32_t)pl->items.size();
+    int64_t rays = build_work_items(p, group.data(), (int)group.size(), j, slot, &pl->items);
+    sd.w1 = (int32_t)pl->items.size();
+    sd.n_rays = rays;
+    sd.step = S->steps_done;
+    sd.beta = beta_of(S, j, group);
+    pl->steps.push_back(sd);
+    S->steps_done++;
+    S->last_group = (int)group.size();
+}
+
+int take_events(csgd_solver* S, int n, int* first) {
+    while (S->ev_pool.size() < S->ev_used + n) {
+        cudaEvent_t e;
+        CSGD_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+        S->ev_pool.push_back(e);
+    }
+    *first = (int)S->ev_used;
+    S->ev_used += n;
+    return CSGD_OK;
+}
+
+int execute_plan(csgd_solver* S, Plan& pl, cudaStream_t s) {
+    const Partition& p = S->P->p;
+    if (pl.ops.empty()) return CSGD_OK;
+    int rc = ensure_sched_capacity(S, (int64_t)pl.items.size(), (int64_t)pl.steps.size(), s);
+    if (rc) return rc;
+    rc = ensure_history(S, S->steps_done, s);
+    if (rc) return rc;
+    if (!pl.items.empty())
+        CSGD_CUDA(cudaMemcpyAsync(S->d_items, pl.items.data(), sizeof(WorkItem) * pl.items.size(),
+                                  cudaMemcpyHostToDevice, s), "upload items");
+    if (!pl.steps.empty())
+        CSGD_CUDA(cudaMemcpyAsync(S->d_steps, pl.steps.data(), sizeof(StepDesc) * pl.steps.size(),
+                                  cudaMemcpyHostToDevice, s), "upload steps");
+    for (const auto& op : pl.ops) {
+        if (op.n < 0) {
+            int e0 = 0;
+            if (S->profiling) {
+                if (take_events(S, 2, &e0)) return CSGD_ERR_CUDA;
+                cudaEventRecord(S->ev_pool[e0], s);
+            }
+            CSGD_CUDA(launch_epoch_close(p.dg, S->sb, S->n_rays, p.max_tile_voxels,
+                                         S->prm.sync == CSGD_SYNC_EPOCH, s), "epoch close");
+            if (S->profiling) {
+                cudaEventRecord(S->ev_pool[e0 + 1], s);
+                S->recs.push_back({3, e0, e0 + 1});
+            }
+            continue;
+        }
+        BatchLaunch b;
+        b.first = op.first;
+        b.nslots = op.n;
+        b.j = op.j;
+        b.max_rays = op.max_rays;
+        b.sync_epoch = S->prm.sync == CSGD_SYNC_EPOCH;
+        cudaEvent_t evs[4];
+        int e0 = 0;
+        if (S->profiling) {
+            if (take_events(S, 4, &e0)) return CSGD_ERR_CUDA;
+            for (int k = 0; k < 4; ++k) evs[k] = S->ev_pool[e0 + k];
+            S->recs.push_back({0, e0, e0 + 1});
+            S->recs.push_back({1, e0 + 1, e0 + 2});
+            S->recs.push_back({2, e0 + 2, e0 + 3});
+        }
+        CSGD_CUDA(launch_batch(p.dg, p.tiles_h[op.j], S->d_items, S->d_steps, b, S->sb,
+                               S->P->sm_count, s, S->profiling ? evs : nullptr), "batch kernels");
+    }
+    return CSGD_OK;
+}
+
+// Append the next `n` scheduled steps (and the epoch closes they cross) to pl.
+void plan_scheduled(csgd_solver* S, Plan* pl, int64_t n, bool close_at_end) {
+    int64_t left = n;
+    while (left > 0) {
+        if (S->queue.empty()) {
+            fill_queue(S);
+            if (S->queue.empty()) break;
+        }
+        // one batch: consecutive steps of the same column block, up to max_slots
+        int j = S->queue.front().j;
+        Plan::Op op{(int)pl->steps.size(), 0, j, 0};
+        while (left > 0 && !S->queue.empty() && op.n < S->max_slots) {
+            QueuedStep qs = S->queue.front();
+            if (qs.j != j) break;
+            S->queue.pop_front();
+            plan_step(S, pl, qs.j, qs.group, op.n);
+            op.max_rays = std::max(op.max_rays, pl->steps.back().n_rays);
+            op.n++;
+            left--;
+            S->epoch_open = true;
+            if (qs.last_in_batch) break;
+        }
+        pl->ops.push_back(op);
+        if (S->queue.empty() && S->epoch_open) {
+            pl->ops.push_back(Plan::Op{0, -1, 0, 0});
+            S->epoch++;
+            S->epoch_open = false;
+        }
+    }
+    if (close_at_end && S->epoch_open) {
+        S->queue.clear();
+        pl->ops.push_back(Plan::Op{0, -1, 0, 0});
+        S->epoch++;
+        S->epoch_open = false;
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// extern "C"
+// ===========================================================================
+extern "C" {
+
+const char* csgd_last_error(void) { return g_err.c_str(); }
+
+const char* csgd_version(void) { return "csgd-gb300 0.1 (sm_103a)"; }
+
+int32_t csgd_geometry_create(const csgd_geometry_desc* desc, csgd_geometry** out) {
+    if (!out) return fail(CSGD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    csgd_geometry* g = new (std::nothrow) csgd_geometry;
+    if (!g) return fail(CSGD_ERR_OOM, "host allocation");
+    std::string err;
+    int rc = geometry_from_desc(desc, &g->g, &err);
+    if (rc) {
+        delete g;
+        return fail(rc, err);
+    }
+    *out = g;
+    return CSGD_OK;
+}
+
+int32_t csgd_geometry_destroy(csgd_geometry* geom) {
+    delete geom;
+    return CSGD_OK;
+}
+
+int32_t csgd_block_partition(const csgd_geometry* geom, const csgd_partition_desc* desc,
+                             csgd_partition** out) {
+    if (!out || !geom) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    csgd_partition* P = new (std::nothrow) csgd_partition;
+    if (!P) return fail(CSGD_ERR_OOM, "host allocation");
+    std::string err;
+    int rc = partition_build(&geom->g, desc, &P->p, &err);
+    if (rc) {
+        delete P;
+        return fail(rc, err);
+    }
+    *out = P;
+    return CSGD_OK;
+}
+
+int32_t csgd_partition_destroy(csgd_partition* P) {
+    if (!P) return CSGD_OK;
+    if (P->on_device) {
+        cudaFree(P->p.d_views);
+        cudaFree(P->p.d_vt);
+        cudaFree(P->p.d_tiles);
+    }
+    delete P;
+    return CSGD_OK;
+}
+
+int32_t csgd_partition_get_info(const csgd_partition* P, csgd_partition_info* info) {
+    if (!P || !info) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    info->m = P->p.m;
+    info->n = P->p.n;
+    info->n_rays = P->p.g->n_rays();
+    info->n_voxels = P->p.g->n_voxels();
+    info->z_floats = P->p.z_floats;
+    return CSGD_OK;
+}
+
+int32_t csgd_partition_probabilities(const csgd_partition* P, double* out) {
+    if (!P || !out) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    memcpy(out, P->p.P.data(), sizeof(double) * P->p.P.size());
+    return CSGD_OK;
+}
+
+int32_t csgd_project_block(const csgd_partition* Pc, const int32_t* row_blocks, int32_t n_rb,
+                           int32_t j, const float* x, float* out, int32_t accumulate,
+                           csgd_stream stream) {
+    csgd_partition* P = const_cast<csgd_partition*>(Pc);
+    if (!P || !x || !out) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    if (j < 0 || j >= P->p.n) return fail(CSGD_ERR_INVALID_ARG, "column block out of range");
+    int rc = check_rows(P->p, row_blocks, n_rb);
+    if (rc) return rc;
+    rc = ensure_device(P);
+    if (rc) return rc;
+    std::vector<WorkItem> items;
+    items_for_rows(P->p, row_blocks, n_rb, j, true, &items);
+    return run_inline(P, items, j, true, x, out, accumulate, (cudaStream_t)stream);
+}
+
+int32_t csgd_backproject_block(const csgd_partition* Pc, const int32_t* row_blocks,
+                               int32_t n_rb, int32_t j, const float* r, float* g,
+                               int32_t accumulate, csgd_stream stream) {
+    csgd_partition* P = const_cast<csgd_partition*>(Pc);
+    if (!P || !r || !g) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    if (j < 0 || j >= P->p.n) return fail(CSGD_ERR_INVALID_ARG, "column block out of range");
+    int rc = check_rows(P->p, row_blocks, n_rb);
+    if (rc) return rc;
+    rc = ensure_device(P);
+    if (rc) return rc;
+    std::vector<WorkItem> items;
+    items_for_rows(P->p, row_blocks, n_rb, j, false, &items);
+    return run_inline(P, items, j, false, r, g, accumulate, (cudaStream_t)stream);
+}
+
+int32_t csgd_project_full(const csgd_partition* Pc, const float* x, float* out,
+                          csgd_stream stream) {
+    csgd_partition* P = const_cast<csgd_partition*>(Pc);
+    if (!P || !x || !out) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    int rc = ensure_device(P);
+    if (rc) return rc;
+    const Partition& p = P->p;
+    cudaStream_t s = (cudaStream_t)stream;
+    CSGD_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * p.g->n_rays(), s), "memset");
+    for (int j = 0; j < p.n; ++j) {
+        std::vector<WorkItem> items;
+        for (int v = 0; v < p.g->n_views; ++v) {
+            const DevVT& e = p.vt(v, j);
+            if (e.u1 <= e.u0 || e.v1 <= e.v0) continue;
+            WorkItem w;
+            w.view = v; w.slot = 0;
+            w.u0 = e.u0; w.u1 = e.u1; w.v0 = e.v0; w.v1 = e.v1;
+            w.ray_off = 0;
+            items.push_back(w);
+        }
+        if (items.empty()) continue;
+        rc = run_inline(P, items, j, true, x, out, 1, s);
+        if (rc) return rc;
+    }
+    return CSGD_OK;
+}
+
+int32_t csgd_schedule_generate(const csgd_partition* P, const csgd_solver_params* params,
+                               int32_t n_epochs, int32_t* out, int64_t capacity, int64_t* len) {
+    if (!P || !len) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    int rc = validate_params(P->p, params);
+    if (rc) return rc;
+    SplitMix64 rng(params->seed);
+    std::vector<int32_t> flat;
+    for (int e = 0; e < n_epochs; ++e) {
+        std::vector<ColumnBatch> ep = epoch_schedule(rng, P->p, *params, e);
+        flat.push_back((int32_t)ep.size());
+        for (auto& cb : ep) {
+            flat.push_back(cb.j);
+            flat.push_back((int32_t)cb.groups.size());
+            for (auto& g : cb.groups) {
+                flat.push_back((int32_t)g.size());
+                for (int i : g) flat.push_back(i);
+            }
+        }
+    }
+    *len = (int64_t)flat.size();
+    if (!out || capacity < (int64_t)flat.size())
+        return fail(CSGD_ERR_INVALID_ARG, "schedule buffer too small");
+    memcpy(out, flat.data(), sizeof(int32_t) * flat.size());
+    return CSGD_OK;
+}
+
+static int64_t footprint(const csgd_partition* P, const csgd_solver_params* prm, int* max_slots,
+                         int64_t* max_rays, int64_t* fwd_blocks, int64_t* n_gg) {
+    const Partition& p = P->p;
+    int64_t ny = p.g->n_rays(), nx = p.g->n_voxels();
+    *max_slots = groups_per_column(p, *prm);
+    *max_rays = max_rays_per_step(p, std::max(1, prm->group_size));
+    *fwd_blocks = std::max<int64_t>(1, (*max_rays + 255) / 256);
+    *n_gg = bp_partials_per_slot(P);
+    int64_t b = 0;
+    b += 4 * (2 * nx);                           // x, xhat
+    b += 4 * (int64_t)p.n;                       // counts
+    b += 4 * (4 * ny);                           // y, r, p, q
+    if (prm->sync == CSGD_SYNC_EPOCH) b += 4 * ny;  // pending residual change
+    b += 4 * std::max<int64_t>(1, p.z_floats);   // z store
+    b += 4 * (int64_t)(*max_slots) * p.max_tile_voxels;  // g per slot
+    b += 8 * (int64_t)(*max_slots) * (*n_gg + *fwd_blocks + 1) + 4 * (*max_slots);
+    return b;
+}
+
+int32_t csgd_solver_footprint_bytes(const csgd_partition* P, const csgd_solver_params* params,
+                                    int64_t* bytes) {
+    if (!P || !bytes) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    int rc = validate_params(P->p, params);
+    if (rc) return rc;
+    int ms;
+    int64_t mr, fb, ng;
+    *bytes = footprint(P, params, &ms, &mr, &fb, &ng);
+    return CSGD_OK;
+}
+
+int32_t csgd_solver_create(const csgd_partition* Pc, const csgd_solver_params* params,
+                           const float* y, csgd_stream stream, csgd_solver** out) {
+    csgd_partition* P = const_cast<csgd_partition*>(Pc);
+    if (!P || !y || !out) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    int rc = validate_params(P->p, params);
+    if (rc) return rc;
+    rc = ensure_device(P);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    csgd_solver* S = new (std::nothrow) csgd_solver;
+    if (!S) return fail(CSGD_ERR_OOM, "host allocation");
+    S->P = P;
+    S->prm = *params;
+    S->n_rays = P->p.g->n_rays();
+    S->n_vox = P->p.g->n_voxels();
+    int64_t mr, fb, ng;
+    footprint(P, params, &S->max_slots, &mr, &fb, &ng);
+    S->max_rays_per_step = mr;
+    SolverBuffers& b = S->sb;
+    memset(&b, 0, sizeof(b));
+    b.max_slots = S->max_slots;
+    b.max_fwd_blocks = (int)fb;
+    b.g_stride = P->p.max_tile_voxels;
+    const Partition& p = P->p;
+#define ALLOC(ptr, bytes, what)                                    \
+    do {                                                           \
+        rc = dmalloc(S, (void**)&(ptr), (bytes), what);            \
+        if (rc) {                                                  \
+            std::string m = g_err;                                 \
+            csgd_solver_destroy(S);                                \
+            return fail(rc, m);                                    \
+        }                                                          \
+    } while (0)
+    ALLOC(b.x, sizeof(float) * S->n_vox, "cudaMalloc(x)");
+    ALLOC(b.xh, sizeof(float) * S->n_vox, "cudaMalloc(xhat)");
+    ALLOC(b.cnt, sizeof(int32_t) * p.n, "cudaMalloc(count)");
+    float* yy = nullptr;
+    ALLOC(yy, sizeof(float) * S->n_rays, "cudaMalloc(y)");
+    b.y = yy;
+    ALLOC(b.r, sizeof(float) * S->n_rays, "cudaMalloc(r)");
+    ALLOC(b.z, sizeof(float) * std::max<int64_t>(1, p.z_floats), "cudaMalloc(z store)");
+    if (params->sync == CSGD_SYNC_EPOCH) ALLOC(b.d, sizeof(float) * S->n_rays, "cudaMalloc(d)");
+    ALLOC(b.p, sizeof(float) * S->n_rays, "cudaMalloc(p)");
+    ALLOC(b.q, sizeof(float) * S->n_rays, "cudaMalloc(q)");
+    ALLOC(b.g, sizeof(float) * b.max_slots * b.g_stride, "cudaMalloc(g)");
+    ALLOC(b.gg_part, sizeof(double) * b.max_slots * ng, "cudaMalloc(gg partials)");
+    ALLOC(b.qq_part, sizeof(double) * b.max_slots * b.max_fwd_blocks, "cudaMalloc(qq partials)");
+    ALLOC(b.counters, sizeof(unsigned) * b.max_slots, "cudaMalloc(counters)");
+    ALLOC(b.mu, sizeof(double) * b.max_slots, "cudaMalloc(mu)");
+    ALLOC(b.nnz, sizeof(unsigned long long), "cudaMalloc(nnz)");
+    ALLOC(b.nnz_slot, sizeof(unsigned long long) * b.max_slots, "cudaMalloc(nnz per slot)");
+    ALLOC(S->d_sq, sizeof(double) * 256, "cudaMalloc(norm partials)");
+#undef ALLOC
+    cudaError_t e = cudaMemcpyAsync(yy, y, sizeof(float) * S->n_rays, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+        csgd_solver_destroy(S);
+        return cuda_fail(e, "copy y");
+    }
+    rc = solver_reset_state(S, s);
+    if (rc == CSGD_OK) rc = ensure_history(S, 1024, s);
+    if (rc == CSGD_OK) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "solver init");
+    }
+    if (rc) {
+        std::string m = g_err;
+        csgd_solver_destroy(S);
+        return fail(rc, m);
+    }
+    *out = S;
+    return CSGD_OK;
+}
+
+int32_t csgd_solver_destroy(csgd_solver* S) {
+    if (!S) return CSGD_OK;
+    for (cudaEvent_t e : S->ev_pool) cudaEventDestroy(e);
+    for (void* p : S->allocs) cudaFree(p);
+    delete S;
+    return CSGD_OK;
+}
+
+int32_t csgd_solver_reset(csgd_solver* S, const float* y, int32_t y_on_host, csgd_stream stream) {
+    if (!S || !y) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CSGD_CUDA(cudaMemcpyAsync((void*)S->sb.y, y, sizeof(float) * S->n_rays,
+                              y_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s),
+              "copy y");
+    return solver_reset_state(S, s);
+}
+
+int32_t csgd_solve_step(csgd_solver* S, const csgd_block_choice* choice, csgd_step_info* info,
+                        csgd_stream stream) {
+    if (!S) return fail(CSGD_ERR_INVALID_ARG, "NULL solver");
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan pl;
+    int64_t step_index = S->steps_done;
+    int j = -1, nrows = 0;
+    if (choice) {
+        const Partition& p = S->P->p;
+        if (choice->j < 0 || choice->j >= p.n)
+            return fail(CSGD_ERR_INVALID_ARG, "column block out of range");
+        int rc = check_rows(p, choice->row_blocks, choice->n_rows);
+        if (rc) return rc;
+        std::vector<int> grp(choice->row_blocks, choice->row_blocks + choice->n_rows);
+        int64_t rays = 0;
+        for (int i : grp) {
+            std::vector<WorkItem> tmp;
+            rays += build_work_items(p, &i, 1, choice->j, 0, &tmp);
+        }
+        if (rays > S->max_rays_per_step)
+            return fail(CSGD_ERR_INVALID_ARG, "group larger than the solver was sized for");
+        Plan::Op op{0, 1, choice->j, 0};
+        plan_step(S, &pl, choice->j, grp, 0);
+        op.max_rays = pl.steps.back().n_rays;
+        pl.ops.push_back(op);
+        S->epoch_open = true;
+        j = choice->j;
+        nrows = choice->n_rows;
+    } else {
+        plan_scheduled(S, &pl, 1, false);
+        if (pl.steps.empty()) return fail(CSGD_ERR_STATE, "schedule has no steps");
+        j = pl.steps[0].j;
+    }
+    int rc = execute_plan(S, pl, s);
+    if (rc) return rc;
+    if (info) {
+        double h[kHistCols] = {0, 0, 0, 0, 0};
+        CSGD_CUDA(cudaMemcpyAsync(h, S->sb.hist + kHistCols * step_index, sizeof(h),
+                                  cudaMemcpyDeviceToHost, s), "read step");
+        CSGD_CUDA(cudaStreamSynchronize(s), "step sync");
+        info->step = step_index;
+        info->j = j;
+        info->n_rows = choice ? nrows : S->last_group;
+        info->beta = h[0];
+        info->gg = h[1];
+        info->qq = h[2];
+        info->mu = h[3];
+    }
+    return CSGD_OK;
+}
+
+int32_t csgd_solve(csgd_solver* S, int64_t n_steps, float* x_out, int32_t x_on_host,
+                   csgd_report* report, int32_t compute_residual, csgd_stream stream) {
+    if (!S || n_steps < 0) return fail(CSGD_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Partition& p = S->P->p;
+    unsigned long long nnz0 = 0;
+    if (report) {
+        CSGD_CUDA(cudaMemcpyAsync(&nnz0, S->sb.nnz, sizeof(nnz0), cudaMemcpyDeviceToHost, s),
+                  "read nnz");
+        CSGD_CUDA(cudaStreamSynchronize(s), "sync");
+    }
+    int64_t steps0 = S->steps_done;
+    Plan pl;
+    plan_scheduled(S, &pl, n_steps, true);
+    int rc = execute_plan(S, pl, s);
+    if (rc) return rc;
+    if (x_out) {
+        if (x_on_host) {
+            if (!S->d_xrow) {
+                rc = dmalloc(S, (void**)&S->d_xrow, sizeof(float) * S->n_vox, "cudaMalloc(x row)");
+                if (rc) return rc;
+            }
+            CSGD_CUDA(launch_tile_to_rowmajor(p.dg, S->sb.x, S->d_xrow, p.max_tile_voxels, s),
+                      "x layout");
+            CSGD_CUDA(cudaMemcpyAsync(x_out, S->d_xrow, sizeof(float) * S->n_vox,
+                                      cudaMemcpyDeviceToHost, s), "x to host");
+        } else {
+            CSGD_CUDA(launch_tile_to_rowmajor(p.dg, S->sb.x, x_out, p.max_tile_voxels, s),
+                      "x layout");
+        }
+    }
+    if (report) {
+        memset(report, 0, sizeof(*report));
+        if (compute_residual) {
+            if (!S->d_xrow) {
+                rc = dmalloc(S, (void**)&S->d_xrow, sizeof(float) * S->n_vox, "cudaMalloc(x row)");
+                if (rc) return rc;
+            }
+            if (!S->d_ax) {
+                rc = dmalloc(S, (void**)&S->d_ax, sizeof(float) * S->n_rays, "cudaMalloc(Ax)");
+                if (rc) return rc;
+            }
+            CSGD_CUDA(launch_tile_to_rowmajor(p.dg, S->sb.x, S->d_xrow, p.max_tile_voxels, s),
+                      "x layout");
+            rc = csgd_project_full(S->P, S->d_xrow, S->d_ax, s);
+            if (rc) return rc;
+            CSGD_CUDA(launch_sq_residual(S->sb.y, S->d_ax, S->n_rays, S->d_sq, s), "norm");
+            double part[256];
+            CSGD_CUDA(cudaMemcpyAsync(part, S->d_sq, sizeof(part), cudaMemcpyDeviceToHost, s),
+                      "read norm");
+            CSGD_CUDA(cudaStreamSynchronize(s), "sync");
+            double ss = 0.0;
+            for (int k = 0; k < 256; ++k) ss += part[k];
+            report->residual_norm = sqrt(ss);
+        }
+        unsigned long long nnz1 = 0;
+        CSGD_CUDA(cudaMemcpyAsync(&nnz1, S->sb.nnz, sizeof(nnz1), cudaMemcpyDeviceToHost, s),
+                  "read nnz");
+        CSGD_CUDA(cudaStreamSynchronize(s), "sync");
+        report->steps = S->steps_done - steps0;
+        report->epochs = S->epoch;
+        report->nnz = (int64_t)(nnz1 - nnz0);
+        report->updates = 3.0 * (double)(nnz1 - nnz0);
+    }
+    return CSGD_OK;
+}
+
+int32_t csgd_solver_history(csgd_solver* S, csgd_step_info* out, int64_t capacity,
+                            int64_t* count) {
+    if (!S || !count) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    int64_t n = std::min<int64_t>(S->steps_done, S->sb.hist_cap);
+    int64_t take = std::min<int64_t>(n, capacity);
+    *count = take;
+    if (take <= 0) return CSGD_OK;
+    std::vector<double> h(kHistCols * take);
+    int64_t start = n - take;
+    CSGD_CUDA(cudaMemcpy(h.data(), S->sb.hist + kHistCols * start, sizeof(double) * kHistCols * take,
+                         cudaMemcpyDeviceToHost), "read history");
+    for (int64_t k = 0; k < take; ++k) {
+        const double* row = &h[kHistCols * k];
+        out[k].step = start + k;
+        out[k].j = -1;
+        out[k].n_rows = -1;
+        out[k].beta = row[0];
+        out[k].gg = row[1];
+        out[k].qq = row[2];
+        out[k].mu = row[3];
+        out[k].nnz = (int64_t)row[4];
+    }
+    return CSGD_OK;
+}
+
+int32_t csgd_solver_profile(csgd_solver* S, int32_t enable) {
+    if (!S) return fail(CSGD_ERR_INVALID_ARG, "NULL solver");
+    S->profiling = enable != 0;
+    return CSGD_OK;
+}
+
+int32_t csgd_solver_profile_read(csgd_solver* S, csgd_kernel_times* out, int32_t reset) {
+    if (!S || !out) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    if (!S->recs.empty()) {
+        CSGD_CUDA(cudaEventSynchronize(S->ev_pool[S->recs.back().e1]), "event sync");
+    }
+    for (const auto& r : S->recs) {
+        float ms = 0.f;
+        CSGD_CUDA(cudaEventElapsedTime(&ms, S->ev_pool[r.e0], S->ev_pool[r.e1]), "elapsed");
+        out->launches[r.kind] += 1;
+        out->ms[r.kind] += ms;
+    }
+    if (reset) {
+        S->recs.clear();
+        S->ev_used = 0;
+    }
+    return CSGD_OK;
+}
+
+}  // extern "C"

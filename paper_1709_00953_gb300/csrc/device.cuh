@@ -1,0 +1,251 @@
+// Device helpers: ray set-up (a1) and incremental Siddon traversal.
+//
+// A_i^j is the length of line i inside voxel j (Sec. II-A).  Every kernel that
+// needs entries of A calls `traverse` with a box of voxels (a whole tile for the
+// forward products, a shared-memory sub-box for the backprojection), so the
+// forward and adjoint operators see bit-identical lengths for the same line and
+// plane: the crossing parameter of a plane is always t = (plane - q) / d
+// evaluated the same way, in tile-centred coordinates.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "common.h"
+
+namespace csgd {
+
+// Tile-centred reference point q and unit direction d of the line through bin
+// (ku, kv) of view V, for the tile whose per (view, tile) constants are E.
+__device__ __forceinline__ void ray_setup(const DevGeom& G, const DevView& V, const DevVT& E,
+                                          int ku, int kv, float q[3], float d[3]) {
+    if (G.kind == FAN_2D_CURVED) {
+        // direction at angle gamma_k from the central ray; the point at the tile
+        // centre's depth D is offset laterally by D (tan gamma_k - tan gamma_k0),
+        // written as D sin(gamma_k - gamma_k0) / (cos gamma_k cos gamma_k0) so that
+        // nothing cancels.
+        float gam = ((float)ku - G.cu) * G.pu;
+        float sg, cg;
+        sincosf(gam, &sg, &cg);
+        float del = (float)(ku - E.k0u) * G.pu;
+        float lat = E.U[0] * sinf(del) * (E.U[1] / cg);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            q[a] = fmaf(lat, V.eu[a], E.B[a]);
+            d[a] = cg * V.dc[a] + sg * V.eu[a];
+        }
+        return;
+    }
+    float du = (float)(ku - E.k0u), dv = (float)(kv - E.k0v);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) q[a] = fmaf(dv, E.V[a], fmaf(du, E.U[a], E.B[a]));
+    if (G.kind == PARALLEL_2D) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) d[a] = V.dc[a];
+        return;
+    }
+    float u = ((float)ku - G.cu) * G.pu;
+    float w = ((float)kv - G.cv) * G.pv;
+    float n2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        d[a] = fmaf(w, V.ev[a], fmaf(u, V.eu[a], V.sdd * V.dc[a]));
+        n2 = fmaf(d[a], d[a], n2);
+    }
+    float inv = 1.0f / sqrtf(n2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] *= inv;
+}
+
+// Continuous detector bin coordinate of a point P (voxel units, grid-centred).
+__device__ __forceinline__ void detector_coord(const DevGeom& G, const DevView& V, const float P[3],
+                                               float* wu, float* wv) {
+    if (G.kind == PARALLEL_2D) {
+        *wu = (P[0] * V.eu[0] + P[1] * V.eu[1]) / G.pu + 0.5f * G.nu;
+        *wv = 0.5f;
+        return;
+    }
+    float r0 = P[0] - V.S[0], r1 = P[1] - V.S[1], r2 = P[2] - V.S[2];
+    float depth = r0 * V.dc[0] + r1 * V.dc[1] + r2 * V.dc[2];
+    float lu = r0 * V.eu[0] + r1 * V.eu[1] + r2 * V.eu[2];
+    if (G.kind == FAN_2D_CURVED) {
+        *wu = atan2f(lu, depth) / G.pu + 0.5f * G.nu;
+        *wv = 0.5f;
+        return;
+    }
+    float lam = V.sdd / depth;
+    *wu = lam * lu / G.pu + 0.5f * G.nu;
+    if (G.dim == 3) {
+        float lv = r0 * V.ev[0] + r1 * V.ev[1] + r2 * V.ev[2];
+        *wv = lam * lv / G.pv + 0.5f * G.nv;
+    } else {
+        *wv = 0.5f;
+    }
+}
+
+// Box of voxels for a traversal: tile-centred lower corner, size, index strides.
+struct Box {
+    float lo[3];
+    int n[3];
+    int stride[3];
+    int base;
+};
+
+// Incremental Siddon traversal of the line q + t d (|d| = 1) through the box.
+// Calls f(index, length) for every voxel the line crosses, in order, with the
+// running linear index base + sum_a i_a * stride_a; lengths are >= 0 (a zero
+// length can occur where the line passes exactly through an edge).  Returns the
+// number of positive lengths.  Indices never leave the box.
+template <int DIM, class F>
+__device__ __forceinline__ int traverse(const float q[3], const float d[3], const Box& b, F&& f) {
+    float tin = -INFINITY, tout = INFINITY;
+    float inv[3];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        if (d[a] != 0.f) {
+            inv[a] = 1.0f / d[a];
+            float t0 = (b.lo[a] - q[a]) * inv[a];
+            float t1 = (b.lo[a] + (float)b.n[a] - q[a]) * inv[a];
+            tin = fmaxf(tin, fminf(t0, t1));
+            tout = fminf(tout, fmaxf(t0, t1));
+        } else {
+            inv[a] = 0.f;
+            if (!(q[a] >= b.lo[a] && q[a] < b.lo[a] + (float)b.n[a])) return 0;
+        }
+    }
+    if (!(tin < tout)) return 0;
+    int i[3], st[3];
+    float pl[3], tn[3];
+    int idx = b.base;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        float pa = d[a] != 0.f ? fmaf(tin, d[a], q[a]) : q[a];
+        int ia = (int)floorf(pa - b.lo[a]);
+        ia = ia < 0 ? 0 : (ia >= b.n[a] ? b.n[a] - 1 : ia);
+        i[a] = ia;
+        st[a] = d[a] > 0.f ? 1 : -1;
+        pl[a] = b.lo[a] + (float)(ia + (d[a] > 0.f ? 1 : 0));
+        tn[a] = d[a] != 0.f ? (pl[a] - q[a]) * inv[a] : INFINITY;
+        idx += ia * b.stride[a];
+    }
+    float tc = tin;
+    int cnt = 0;
+    if (DIM == 2) {
+        float tx = tn[0], ty = tn[1];
+        int ix = i[0], iy = i[1];
+        const float px0 = pl[0], py0 = pl[1];
+        float px = px0, py = py0;
+        for (;;) {
+            bool bx = tx <= ty;
+            float t = fminf(bx ? tx : ty, tout);
+            float len = fmaxf(t - tc, 0.f);
+            f(idx, len);
+            cnt += len > 0.f;
+            if (t >= tout) break;
+            tc = t;
+            if (bx) {
+                ix += st[0];
+                if ((unsigned)ix >= (unsigned)b.n[0]) break;
+                idx += st[0] * b.stride[0];
+                px += (float)st[0];
+                tx = (px - q[0]) * inv[0];
+            } else {
+                iy += st[1];
+                if ((unsigned)iy >= (unsigned)b.n[1]) break;
+                idx += st[1] * b.stride[1];
+                py += (float)st[1];
+                ty = (py - q[1]) * inv[1];
+            }
+        }
+    } else {
+        float tx = tn[0], ty = tn[1], tz = tn[2];
+        int ix = i[0], iy = i[1], iz = i[2];
+        float px = pl[0], py = pl[1], pz = pl[2];
+        for (;;) {
+            bool bx = tx <= ty && tx <= tz;
+            bool by = !bx && ty <= tz;
+            float tm = bx ? tx : (by ? ty : tz);
+            float t = fminf(tm, tout);
+            float len = fmaxf(t - tc, 0.f);
+            f(idx, len);
+            cnt += len > 0.f;
+            if (t >= tout) break;
+            tc = t;
+            if (bx) {
+                ix += st[0];
+                if ((unsigned)ix >= (unsigned)b.n[0]) break;
+                idx += st[0] * b.stride[0];
+                px += (float)st[0];
+                tx = (px - q[0]) * inv[0];
+            } else if (by) {
+                iy += st[1];
+                if ((unsigned)iy >= (unsigned)b.n[1]) break;
+                idx += st[1] * b.stride[1];
+                py += (float)st[1];
+                ty = (py - q[1]) * inv[1];
+            } else {
+                iz += st[2];
+                if ((unsigned)iz >= (unsigned)b.n[2]) break;
+                idx += st[2] * b.stride[2];
+                pz += (float)st[2];
+                tz = (pz - q[2]) * inv[2];
+            }
+        }
+    }
+    return cnt;
+}
+
+// Compensated (Kahan) accumulator for the FP32 ray sums.
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        float y = v - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum in a fixed order (deterministic); every thread gets the result.
+// `sh` must hold blockDim.x / 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += sh[k];
+    return s;
+}
+
+// Ray index of bin (ku, kv) of view v.
+__device__ __forceinline__ int64_t ray_index(const DevGeom& G, int v, int ku, int kv) {
+    return ((int64_t)v * G.nv + kv) * G.nu + ku;
+}
+
+// The work item holding ray k of a slot whose items are [w0, w1) (binary search
+// on the items' ray offsets).
+__device__ __forceinline__ int find_item(const WorkItem* items, int w0, int w1, int64_t k) {
+    int lo = w0, hi = w1 - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (items[mid].ray_off <= k) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace csgd

@@ -1,0 +1,219 @@
+"""GPU parity: the CUDA block operators and solver against the FP64 oracle.
+
+Tolerances (derived in DESIGN.md, "Parity and tolerances"):
+
+* per ray of a forward product and per voxel of a backprojection:
+  |gpu - oracle| <= 1e-5 * (|A| |v|)  +  TAU_GEOM * h * max|v|
+  The first term is the 1e-5 relative bound on a ray sum, taken against the sum
+  of absolute terms (the usual forward-error scale of a dot product; it equals
+  the ray sum itself for non-negative v).  The second term covers the FP32
+  geometry: the GPU places each line to within ~1e-6 voxel in tile-centred
+  coordinates, so an entry can move by up to TAU_GEOM * h at a grazing corner.
+* the step length mu of every step: 1e-5 relative;
+* the reconstruction after a fixed number of steps: RMSE(x_gpu, x_oracle) <= 1e-4.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import blocks as OB  # noqa: E402
+from oracle import siddon as OSd  # noqa: E402
+from oracle.blocks import Partition as OPart  # noqa: E402
+from oracle.geometry import Geometry as OGeom  # noqa: E402
+from oracle.solver import OracleSolver  # noqa: E402
+from synth import configs as C  # noqa: E402
+from synth import data as D  # noqa: E402
+
+TAU_GEOM = 2.0 ** -14
+REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def csgd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_00953_gb300 import build as B
+    B.build()
+    from paper_1709_00953_gb300 import csgd as M
+    return M
+
+
+def _pair(csgd, cfg):
+    g = csgd.Geometry(cfg["geom"])
+    p = csgd.Partition(g, **cfg["part"])
+    og = OGeom(**cfg["geom"])
+    op = OPart(og, cfg["part"]["tiles"], cfg["part"]["view_blocks"], cfg["part"]["det_blocks"])
+    return p, op
+
+
+def _abs_forward(op, rows_blocks, j, v):
+    g = op.geom
+    rows = op.rows_of(rows_blocks)
+    o, d = g.rays(rows)
+    lo, hi = op.tile_box(j)
+    return OSd.project_box(g.grid, o, d, lo, hi, np.abs(v))
+
+
+def _abs_back(op, rows_blocks, j, r_rows):
+    g = op.geom
+    rows = op.rows_of(rows_blocks)
+    o, d = g.rays(rows)
+    lo, hi = op.tile_box(j)
+    return OSd.backproject_box(g.grid, o, d, lo, hi, np.abs(r_rows))
+
+
+CASES = {
+    "parallel64": C.parallel2d_64(),
+    "fan_curved_ragged": C.small_fan2d(n=96, views=48, nu=144, tiles=(3, 3), vb=4, du=2),
+    "fan_flat_ragged": C.small_fan2d(n=80, views=40, nu=120, tiles=(2, 3), vb=4, du=3,
+                                     curved=False),
+    "cone_ragged": C.small_cone3d(n=24, views=12, nd=40, tiles=(2, 2, 3), du=2, dv=2),
+}
+
+
+def _groups(op):
+    m, n = op.n_row_blocks, op.n_col_blocks
+    return [([0], 0), ([m - 1], n - 1), (list(range(0, m, 2)), n // 2), ([m // 2], 1 % n)]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_project_block_parity(csgd, name):
+    cfg = CASES[name]
+    p, op = _pair(csgd, cfg)
+    g = op.geom
+    rng = np.random.default_rng(1)
+    x = rng.random(g.grid.size)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    for grp, j in _groups(op):
+        out = torch.full((g.n_rays,), -7.0, dtype=torch.float32, device="cuda")
+        csgd.project_block(p, grp, j, xt, out)
+        rows, ref = OB.project_block(op, grp, j, x.astype(np.float32).astype(np.float64))
+        got = out.cpu().numpy().astype(np.float64)
+        # rows outside the union are untouched
+        mask = np.ones(g.n_rays, bool)
+        mask[rows] = False
+        assert np.all(got[mask] == -7.0)
+        err = np.abs(got[rows] - ref)
+        tol = REL * _abs_forward(op, grp, j, x) + TAU_GEOM * g.h * np.abs(x).max()
+        assert np.all(err <= tol), (name, grp, j, float((err / tol).max()))
+        assert ref.max() > 0
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_project_block_accumulate(csgd, name):
+    cfg = CASES[name]
+    p, op = _pair(csgd, cfg)
+    g = op.geom
+    x = torch.rand(g.grid.size, dtype=torch.float32, device="cuda")
+    a = torch.zeros(g.n_rays, dtype=torch.float32, device="cuda")
+    for j in range(op.n_col_blocks):
+        csgd.project_block(p, list(range(op.n_row_blocks)), j, x, a, accumulate=True)
+    full = torch.zeros_like(a)
+    csgd.project_full(p, x, full)
+    torch.testing.assert_close(a, full, rtol=1e-6, atol=1e-5)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_backproject_block_parity(csgd, name):
+    cfg = CASES[name]
+    p, op = _pair(csgd, cfg)
+    g = op.geom
+    rng = np.random.default_rng(2)
+    r = rng.standard_normal(g.n_rays).astype(np.float32)
+    rt = torch.tensor(r, device="cuda")
+    for grp, j in _groups(op):
+        gv = torch.full((g.grid.size,), 3.0, dtype=torch.float32, device="cuda")
+        csgd.backproject_block(p, grp, j, rt, gv)
+        rows = op.rows_of(grp)
+        ref = OB.backproject_block(op, grp, j, r[rows].astype(np.float64))
+        got = gv.cpu().numpy().astype(np.float64)
+        vox = op.tile_voxels(j)
+        mask = np.ones(g.grid.size, bool)
+        mask[vox] = False
+        assert np.all(got[mask] == 3.0)
+        err = np.abs(got[vox] - ref[vox])
+        tol = REL * _abs_back(op, grp, j, r[rows])[vox] + TAU_GEOM * g.h * np.abs(r).max()
+        assert np.all(err <= tol), (name, grp, j, float((err / tol).max()))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_identity_on_gpu(csgd, name):
+    """<A_I^J x, r> = <x, (A_I^J)^T r>: the two kernels use identical lengths."""
+    cfg = CASES[name]
+    p, op = _pair(csgd, cfg)
+    g = op.geom
+    x = torch.randn(g.grid.size, dtype=torch.float32, device="cuda")
+    r = torch.randn(g.n_rays, dtype=torch.float32, device="cuda")
+    for grp, j in _groups(op):
+        ax = torch.zeros(g.n_rays, dtype=torch.float32, device="cuda")
+        atr = torch.zeros(g.grid.size, dtype=torch.float32, device="cuda")
+        csgd.project_block(p, grp, j, x, ax)
+        csgd.backproject_block(p, grp, j, r, atr)
+        rows = torch.tensor(op.rows_of(grp), device="cuda")
+        vox = torch.tensor(op.tile_voxels(j), device="cuda")
+        lhs = torch.dot(ax[rows].double(), r[rows].double()).item()
+        rhs = torch.dot(x[vox].double(), atr[vox].double()).item()
+        scale = torch.dot(ax[rows].double().abs(), r[rows].double().abs()).item()
+        assert abs(lhs - rhs) <= 1e-6 * scale
+
+
+def _solver_pair(csgd, cfg, steps):
+    y, _ = D.make_data(cfg)
+    p, op = _pair(csgd, cfg)
+    yt = torch.tensor(y, device="cuda")
+    s = csgd.Solver(p, cfg["solver"], yt)
+    x_gpu = torch.zeros(op.geom.grid.size, dtype=torch.float32, device="cuda")
+    rep = s.solve(steps, x_gpu, residual=True)
+    hist = s.history()
+    o = OracleSolver(op, cfg["solver"], y.astype(np.float64))
+    x_ref = o.run(steps)
+    return x_gpu.cpu().numpy().astype(np.float64), x_ref, hist, o, rep, y
+
+
+@pytest.mark.parametrize("name,steps", [("parallel64", 400), ("fan_curved_ragged", 60),
+                                        ("fan_flat_ragged", 40), ("cone_ragged", 30)])
+def test_solver_parity(csgd, name, steps):
+    cfg = CASES[name]
+    x_gpu, x_ref, hist, o, rep, y = _solver_pair(csgd, cfg, steps)
+    assert rep["steps"] == steps
+    assert len(hist) == steps == len(o.log)
+    mu_g = np.array([h["mu"] for h in hist])
+    mu_o = np.array([l["mu"] for l in o.log])
+    beta_g = np.array([h["beta"] for h in hist])
+    beta_o = np.array([l["beta"] for l in o.log])
+    np.testing.assert_allclose(beta_g, beta_o, rtol=1e-12)
+    np.testing.assert_allclose(mu_g, mu_o, rtol=REL, atol=1e-12)
+    rmse = float(np.sqrt(np.mean((x_gpu - x_ref) ** 2)))
+    assert rmse <= 1e-4, rmse
+    assert np.abs(x_ref).max() > 0
+    # the library's residual norm ||y - A x|| matches the oracle's for its own x
+    from oracle import metrics
+    ax = metrics.forward_full(o.part.geom, x_gpu)
+    np.testing.assert_allclose(rep["residual_norm"], np.linalg.norm(y - ax), rtol=1e-4)
+
+
+def test_epoch_sync_parity(csgd):
+    cfg = dict(CASES["fan_curved_ragged"])
+    cfg["solver"] = dict(cfg["solver"], sync=1, sampling=3, theta_step=0.25)
+    x_gpu, x_ref, hist, o, rep, y = _solver_pair(csgd, cfg, 50)
+    mu_g = np.array([h["mu"] for h in hist])
+    mu_o = np.array([l["mu"] for l in o.log])
+    np.testing.assert_allclose(mu_g, mu_o, rtol=REL, atol=1e-12)
+    assert float(np.sqrt(np.mean((x_gpu - x_ref) ** 2))) <= 1e-4
+
+
+def test_explicit_block_choice(csgd):
+    cfg = CASES["cone_ragged"]
+    y, _ = D.make_data(cfg)
+    p, op = _pair(csgd, cfg)
+    s = csgd.Solver(p, cfg["solver"], torch.tensor(y, device="cuda"))
+    info = s.step(j=3, row_blocks=[1, 5, 7])
+    o = OracleSolver(op, cfg["solver"], y.astype(np.float64))
+    ref = o.step(3, [1, 5, 7])
+    assert info["n_rows"] == 3
+    np.testing.assert_allclose(info["mu"], ref["mu"], rtol=REL)
+    np.testing.assert_allclose(info["gg"], ref["gg"], rtol=REL)
+    np.testing.assert_allclose(info["qq"], ref["qq"], rtol=REL)
