@@ -310,7 +310,11 @@ def run_gpu(args, cfg, world, rank, local):
             "peak_basis": "FP32 FMA: %d SMs x %d lanes x 2 x %.0f MHz (median SM clock of this run)"
                           % (sm_count, FP32_LANES_PER_SM, mhz),
             "flop_per_nnz": ALG_FLOP[dom]}
-    launches = int(sum(v["launches"] for v in prof.values()))
+    # per batch: ray table + backprojection, dual forward, epilogue; per epoch close:
+    # averaging (+ pending-residual apply under epoch sync)
+    close_kernels = 2 if cfg["solver"].get("sync", 0) == 1 else 1
+    launches = int(2 * prof["backproject"]["launches"] + prof["forward_dual"]["launches"]
+                   + prof["epilogue"]["launches"] + close_kernels * prof["epoch_close"]["launches"])
     kernels = {k: {"launches": int(v["launches"]), "ms": v["ms"],
                    "share": (v["ms"] / total_ms if total_ms else 0.0)} for k, v in kern.items()}
 

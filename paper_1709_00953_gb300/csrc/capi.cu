@@ -144,7 +144,7 @@ int run_inline(csgd_partition* P, const std::vector<WorkItem>& items, int j, boo
         int acc = (first ? accumulate : 1);
         cudaError_t e;
         if (forward) {
-            e = launch_project_inline(p.dg, *it, in, out, accumulate, s);
+            e = launch_project_inline(p.dg, *it, in, out, accumulate, P->sm_count, s);
         } else if (cnt == 0) {
             // no rays: g = 0 on the tile unless accumulating
             if (!acc) {
@@ -152,12 +152,20 @@ int run_inline(csgd_partition* P, const std::vector<WorkItem>& items, int j, boo
                 memset(&empty.step, 0, sizeof(empty.step));
                 empty.step.j = j;
                 empty.n = 0;
-                e = launch_backproject_inline(p.dg, p.tiles_h[j], empty, in, out, 0, P->sm_count, s);
+                e = launch_backproject_inline(p.dg, p.tiles_h[j], empty, in, out, 0, nullptr,
+                                              P->sm_count, s);
             } else {
                 e = cudaSuccess;
             }
         } else {
-            e = launch_backproject_inline(p.dg, p.tiles_h[j], *it, in, out, acc, P->sm_count, s);
+            RayRec* table = nullptr;
+            e = cudaMallocAsync((void**)&table, sizeof(RayRec) * (size_t)rays, s);
+            if (e == cudaSuccess) {
+                e = launch_backproject_inline(p.dg, p.tiles_h[j], *it, in, out, acc, table,
+                                              P->sm_count, s);
+                cudaError_t e2 = cudaFreeAsync(table, s);
+                if (e == cudaSuccess) e = e2;
+            }
         }
         if (e != cudaSuccess) {
             rc = cuda_fail(e, forward ? "project kernel" : "backproject kernel");
@@ -281,13 +289,8 @@ int validate_params(const Partition& p, const csgd_solver_params* prm) {
 }
 
 int64_t bp_partials_per_slot(const csgd_partition* P) {
-    const Partition& p = P->p;
-    int64_t best = 1;
-    for (int j = 0; j < p.n; ++j) {
-        BPPlan pl = plan_backprojection(p.dg, p.tiles_h[j], 1, std::max(1, P->sm_count));
-        best = std::max<int64_t>(best, (int64_t)pl.nsb * pl.C);
-    }
-    return best;
+    // one g^T g partial per backprojection CTA of a slot (one thread per voxel)
+    return std::max<int64_t>(1, (P->p.max_tile_voxels + 255) / 256);
 }
 
 int solver_reset_state(csgd_solver* S, cudaStream_t s) {
@@ -653,7 +656,7 @@ static int64_t footprint(const csgd_partition* P, const csgd_solver_params* prm,
     int64_t ny = p.g->n_rays(), nx = p.g->n_voxels();
     *max_slots = groups_per_column(p, *prm);
     *max_rays = max_rays_per_step(p, std::max(1, prm->group_size));
-    *fwd_blocks = std::max<int64_t>(1, (*max_rays + 255) / 256);
+    *fwd_blocks = std::max<int64_t>(1, (*max_rays * 4 + 255) / 256);
     *n_gg = bp_partials_per_slot(P);
     int64_t b = 0;
     b += 4 * (2 * nx);                           // x, xhat
@@ -662,6 +665,7 @@ static int64_t footprint(const csgd_partition* P, const csgd_solver_params* prm,
     if (prm->sync == CSGD_SYNC_EPOCH) b += 4 * ny;  // pending residual change
     b += 4 * std::max<int64_t>(1, p.z_floats);   // z store
     b += 4 * (int64_t)(*max_slots) * p.max_tile_voxels;  // g per slot
+    b += (int64_t)sizeof(RayRec) * (*max_slots) * (*max_rays);  // ray tables
     b += 8 * (int64_t)(*max_slots) * (*n_gg + *fwd_blocks + 1) + 4 * (*max_slots);
     return b;
 }
@@ -701,6 +705,8 @@ int32_t csgd_solver_create(const csgd_partition* Pc, const csgd_solver_params* p
     b.max_slots = S->max_slots;
     b.max_fwd_blocks = (int)fb;
     b.g_stride = P->p.max_tile_voxels;
+    b.gg_stride = (int)ng;
+    b.table_stride = std::max<int64_t>(1, mr);
     const Partition& p = P->p;
 #define ALLOC(ptr, bytes, what)                                    \
     do {                                                           \
@@ -724,6 +730,7 @@ int32_t csgd_solver_create(const csgd_partition* Pc, const csgd_solver_params* p
     ALLOC(b.q, sizeof(float) * S->n_rays, "cudaMalloc(q)");
     ALLOC(b.g, sizeof(float) * b.max_slots * b.g_stride, "cudaMalloc(g)");
     ALLOC(b.gg_part, sizeof(double) * b.max_slots * ng, "cudaMalloc(gg partials)");
+    ALLOC(b.table, sizeof(RayRec) * b.max_slots * b.table_stride, "cudaMalloc(ray tables)");
     ALLOC(b.qq_part, sizeof(double) * b.max_slots * b.max_fwd_blocks, "cudaMalloc(qq partials)");
     ALLOC(b.counters, sizeof(unsigned) * b.max_slots, "cudaMalloc(counters)");
     ALLOC(b.mu, sizeof(double) * b.max_slots, "cudaMalloc(mu)");

@@ -36,6 +36,9 @@ struct DevVT {
     float V[3];    // Q step per v bin
     int32_t k0u, k0v;
     int32_t u0, u1, v0, v1;  // bins [u0,u1) x [v0,v1) whose rays may meet the tile
+    float hw_u, hw_v;  // half-width (bins) of the shadow of one voxel of the tile:
+                       // the bins whose lines can meet a voxel are within hw of the
+                       // bin coordinate of the voxel's centre
     int64_t zoff;  // start of this rectangle's slice of the z store
 };
 
@@ -65,6 +68,16 @@ struct DevGeom {
     const DevView* views;
     const DevVT* vt;       // [view][tile]
     const DevTile* tiles;
+};
+
+// Per-ray table of one launch (ray set-up done once, read by the
+// backprojection): tile-centred point q, reciprocal direction 1/d (infinite
+// where d = 0) and the residual r of the ray.
+struct RayRec {
+    float q[3];
+    float r;
+    float inv[3];
+    float pad;
 };
 
 // One step of the solver as the kernels see it.

@@ -91,34 +91,47 @@ struct Box {
     int base;
 };
 
-// Incremental Siddon traversal of the line q + t d (|d| = 1) through the box.
-// Calls f(index, length) for every voxel the line crosses, in order, with the
-// running linear index base + sum_a i_a * stride_a; lengths are >= 0 (a zero
-// length can occur where the line passes exactly through an edge).  Returns the
-// number of positive lengths.  Indices never leave the box.
-template <int DIM, class F>
-__device__ __forceinline__ int traverse(const float q[3], const float d[3], const Box& b, F&& f) {
-    float tin = -INFINITY, tout = INFINITY;
-    float inv[3];
+// Parameter interval [tin, tout) of the line q + t d (|d| = 1) inside the box;
+// false if the line misses it.
+template <int DIM>
+__device__ __forceinline__ bool clip(const float q[3], const float d[3], const Box& b, float* tin,
+                                     float* tout) {
+    float t0 = -INFINITY, t1 = INFINITY;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         if (d[a] != 0.f) {
-            inv[a] = 1.0f / d[a];
-            float t0 = (b.lo[a] - q[a]) * inv[a];
-            float t1 = (b.lo[a] + (float)b.n[a] - q[a]) * inv[a];
-            tin = fmaxf(tin, fminf(t0, t1));
-            tout = fminf(tout, fmaxf(t0, t1));
-        } else {
-            inv[a] = 0.f;
-            if (!(q[a] >= b.lo[a] && q[a] < b.lo[a] + (float)b.n[a])) return 0;
+            float inv = 1.0f / d[a];
+            float ta = (b.lo[a] - q[a]) * inv;
+            float tb = (b.lo[a] + (float)b.n[a] - q[a]) * inv;
+            t0 = fmaxf(t0, fminf(ta, tb));
+            t1 = fminf(t1, fmaxf(ta, tb));
+        } else if (!(q[a] >= b.lo[a] && q[a] < b.lo[a] + (float)b.n[a])) {
+            return false;
         }
     }
-    if (!(tin < tout)) return 0;
+    *tin = t0;
+    *tout = t1;
+    return t0 < t1;
+}
+
+// Incremental Siddon walk of the line q + t d (|d| = 1) through the box over
+// t in [tin, tout] (inside the box).  Calls f(index, length) for every voxel the
+// line crosses, in order, with the running linear index base + sum_a i_a *
+// stride_a; lengths are >= 0 (a zero length can occur where the line passes
+// exactly through an edge).  A plane crossing is always evaluated as
+// (plane - q) / d, so the lengths do not depend on which box or sub-range the
+// walk runs over.  Returns the number of positive lengths.  Indices never
+// leave the box, which also bounds the number of iterations.
+template <int DIM, class F>
+__device__ __forceinline__ int walk(const float q[3], const float d[3], const Box& b, float tin,
+                                    float tout, F&& f) {
+    float inv[3];
     int i[3], st[3];
     float pl[3], tn[3];
     int idx = b.base;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
+        inv[a] = d[a] != 0.f ? 1.0f / d[a] : 0.f;
         float pa = d[a] != 0.f ? fmaf(tin, d[a], q[a]) : q[a];
         int ia = (int)floorf(pa - b.lo[a]);
         ia = ia < 0 ? 0 : (ia >= b.n[a] ? b.n[a] - 1 : ia);
@@ -133,8 +146,7 @@ __device__ __forceinline__ int traverse(const float q[3], const float d[3], cons
     if (DIM == 2) {
         float tx = tn[0], ty = tn[1];
         int ix = i[0], iy = i[1];
-        const float px0 = pl[0], py0 = pl[1];
-        float px = px0, py = py0;
+        float px = pl[0], py = pl[1];
         for (;;) {
             bool bx = tx <= ty;
             float t = fminf(bx ? tx : ty, tout);
@@ -193,6 +205,14 @@ __device__ __forceinline__ int traverse(const float q[3], const float d[3], cons
         }
     }
     return cnt;
+}
+
+// Whole traversal of the box: clip, then walk.
+template <int DIM, class F>
+__device__ __forceinline__ int traverse(const float q[3], const float d[3], const Box& b, F&& f) {
+    float tin, tout;
+    if (!clip<DIM>(q, d, b, &tin, &tout)) return 0;
+    return walk<DIM>(q, d, b, tin, tout, f);
 }
 
 // Compensated (Kahan) accumulator for the FP32 ray sums.

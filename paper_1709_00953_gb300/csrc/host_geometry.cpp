@@ -423,6 +423,42 @@ int partition_build(const Geometry* gp, const csgd_partition_desc* d, Partition*
             e.v1 = v1;
             e.zoff = zoff;
             zoff += (int64_t)(u1 - u0) * (v1 - v0);
+            // Half-width of a voxel's shadow, in bins.  Neighbouring lines of one
+            // detector row are at least `spacing` apart everywhere in the tile (lines
+            // of a fan meet at the source at an angle of at least `ang` per bin, and
+            // every point of the tile is at least dmin from the source), so the lines
+            // within half a voxel diagonal of a voxel's centre lie within
+            // (diagonal / 2) / spacing bins of the line through the centre.
+            {
+                double dmin = 0.0;
+                if (g.kind != CSGD_PARALLEL_2D) {
+                    double d2 = 0.0;
+                    for (int a = 0; a < g.dim; ++a) {
+                        double lo = t.T[a] - 0.5 * t.n[a], hi = t.T[a] + 0.5 * t.n[a];
+                        double c = std::min(std::max(f.S[a], lo), hi);
+                        d2 += (f.S[a] - c) * (f.S[a] - c);
+                    }
+                    dmin = sqrt(d2);
+                }
+                double umax = 0.5 * g.nu * pu_v;
+                double vmax = g.dim == 3 ? 0.5 * g.nv * pv_v : 0.0;
+                auto spacing_of = [&](double pitch) {
+                    if (g.kind == CSGD_PARALLEL_2D) return pitch;
+                    double ang = g.kind == CSGD_FAN_2D_CURVED
+                                     ? pitch
+                                     : pitch * f.sdd / (f.sdd * f.sdd + umax * umax + vmax * vmax);
+                    return dmin * sin(std::min(ang, 1.0));
+                };
+                double half_diag = 0.5 * sqrt((double)g.dim) * 1.02;
+                double su = spacing_of(pu_v);
+                e.hw_u = (float)(su > 0 ? half_diag / su + 0.01 : 1e6);
+                if (g.dim == 3) {
+                    double sv = spacing_of(pv_v);
+                    e.hw_v = (float)(sv > 0 ? half_diag / sv + 0.01 : 1e6);
+                } else {
+                    e.hw_v = 0.f;
+                }
+            }
             // ray constants (voxel units, tile-centred)
             double T[3] = {t.T[0], t.T[1], t.T[2]};
             if (g.kind == CSGD_PARALLEL_2D) {

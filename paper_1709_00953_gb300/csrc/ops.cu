@@ -28,7 +28,6 @@ namespace {
 constexpr int kFwdThreads = 256;
 constexpr int kBPThreads = 256;
 constexpr int kEpiThreads = 256;
-constexpr int kMaxSubboxFloats = 16384;  // 64 KB of shared memory per CTA
 
 __device__ __forceinline__ Box tile_box(const DevTile& t, int dim, int base, int s1, int s2) {
     Box b;
@@ -57,40 +56,64 @@ struct FwdSolverArgs {
     SolverBuffers sb;
 };
 
-template <int DIM>
+// Rays of one slot are split among L consecutive lanes by parameter range: every
+// lane walks 1/L of the ray's chord through the tile and the L partial sums are
+// combined with warp shuffles, so that short chains of dependent gathers keep
+// more warps in flight.
+template <int L>
+__device__ __forceinline__ float lane_sum(float v) {
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int DIM, int L>
 __device__ __forceinline__ void forward_single(const DevGeom& G, const WorkItem* items,
                                                const StepDesc& sd, const float* x, float* out,
                                                int accumulate) {
     const DevTile t = G.tiles[sd.j];
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= sd.n_rays) return;
-    int w = find_item(items, sd.w0, sd.w1, k);
-    const WorkItem it = items[w];
-    int64_t within = k - it.ray_off;
-    int wu = it.u1 - it.u0;
-    int ku = it.u0 + (int)(within % wu);
-    int kv = it.v0 + (int)(within / wu);
-    const DevView V = G.views[it.view];
-    const DevVT E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
-    float q[3], d[3];
-    ray_setup(G, V, E, ku, kv, q, d);
-    int base = (t.lo[2] * G.ny + t.lo[1]) * G.nx + t.lo[0];
-    Box b = tile_box(t, DIM, base, G.nx, G.nx * G.ny);
-    Kahan acc;
-    traverse<DIM>(q, d, b, [&](int idx, float len) { acc.add(len * __ldg(x + idx)); });
-    int64_t ray = ray_index(G, it.view, ku, kv);
-    float v = G.h * (acc.s - acc.c);
-    out[ray] = accumulate ? out[ray] + v : v;
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t k = gid / L;
+    const int sub = (int)(gid % L);
+    const bool active = k < sd.n_rays;
+    float part = 0.f;
+    int64_t ray = 0;
+    if (active) {
+        int w = find_item(items, sd.w0, sd.w1, k);
+        const WorkItem it = items[w];
+        int64_t within = k - it.ray_off;
+        int wu = it.u1 - it.u0;
+        int ku = it.u0 + (int)(within % wu);
+        int kv = it.v0 + (int)(within / wu);
+        const DevView V = G.views[it.view];
+        const DevVT E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
+        float q[3], d[3];
+        ray_setup(G, V, E, ku, kv, q, d);
+        int base = (t.lo[2] * G.ny + t.lo[1]) * G.nx + t.lo[0];
+        Box b = tile_box(t, DIM, base, G.nx, G.nx * G.ny);
+        float tin, tout;
+        if (clip<DIM>(q, d, b, &tin, &tout)) {
+            float dt = (tout - tin) * (1.0f / L);
+            float t0 = sub == 0 ? tin : fmaf((float)sub, dt, tin);
+            float t1 = sub == L - 1 ? tout : fmaf((float)(sub + 1), dt, tin);
+            Kahan acc;
+            walk<DIM>(q, d, b, t0, t1, [&](int idx, float len) { acc.add(len * __ldg(x + idx)); });
+            part = acc.s - acc.c;
+        }
+        ray = ray_index(G, it.view, ku, kv);
+    }
+    float v = G.h * lane_sum<L>(part);
+    if (active && sub == 0) out[ray] = accumulate ? out[ray] + v : v;
 }
 
-template <int DIM>
+template <int DIM, int L>
 __global__ void __launch_bounds__(kFwdThreads) k_project_inline(
     const DevGeom G, const __grid_constant__ InlineItems it, const float* __restrict__ x,
     float* __restrict__ out, int accumulate) {
-    forward_single<DIM>(G, it.items, it.step, x, out, accumulate);
+    forward_single<DIM, L>(G, it.items, it.step, x, out, accumulate);
 }
 
-template <int DIM>
+template <int DIM, int L>
 __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArgs a) {
     __shared__ double sh[kFwdThreads / 32];
     __shared__ int last;
@@ -100,10 +123,14 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
     const DevTile t = G.tiles[sd.j];
     const float* __restrict__ xj = a.sb.x + t.voff;
     const float* __restrict__ gj = a.sb.g + (int64_t)slot * a.sb.g_stride;
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double qq = 0.0;
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t k = gid / L;
+    const int sub = (int)(gid % L);
+    const bool active = k < sd.n_rays;
+    float pp = 0.f, qp = 0.f;
     long long nz = 0;
-    if (k < sd.n_rays) {
+    int64_t ray = 0;
+    if (active) {
         int w = find_item(a.items, sd.w0, sd.w1, k);
         const WorkItem it = a.items[w];
         int64_t within = k - it.ray_off;
@@ -115,14 +142,25 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
         float q[3], d[3];
         ray_setup(G, V, E, ku, kv, q, d);
         Box b = tile_box(t, DIM, 0, t.n[0], t.n[0] * t.n[1]);
-        Kahan ax, ag;
-        nz = traverse<DIM>(q, d, b, [&](int idx, float len) {
-            ax.add(len * __ldg(xj + idx));
-            ag.add(len * __ldg(gj + idx));
-        });
-        int64_t ray = ray_index(G, it.view, ku, kv);
-        float pv = G.h * (ax.s - ax.c);
-        float qv = G.h * (ag.s - ag.c);
+        float tin, tout;
+        if (clip<DIM>(q, d, b, &tin, &tout)) {
+            float dt = (tout - tin) * (1.0f / L);
+            float t0 = sub == 0 ? tin : fmaf((float)sub, dt, tin);
+            float t1 = sub == L - 1 ? tout : fmaf((float)(sub + 1), dt, tin);
+            Kahan ax, ag;
+            nz = walk<DIM>(q, d, b, t0, t1, [&](int idx, float len) {
+                ax.add(len * __ldg(xj + idx));
+                ag.add(len * __ldg(gj + idx));
+            });
+            pp = ax.s - ax.c;
+            qp = ag.s - ag.c;
+        }
+        ray = ray_index(G, it.view, ku, kv);
+    }
+    float pv = G.h * lane_sum<L>(pp);
+    float qv = G.h * lane_sum<L>(qp);
+    double qq = 0.0;
+    if (active && sub == 0) {
         a.sb.p[ray] = pv;
         a.sb.q[ray] = qv;
         qq = (double)qv * (double)qv;
@@ -147,7 +185,8 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
             qs += __ldcg(a.sb.qq_part + (int64_t)slot * a.sb.max_fwd_blocks + bb);
         const int ngg = a.n_gg;
         double gs = 0.0;
-        for (int bb = 0; bb < ngg; ++bb) gs += __ldcg(a.sb.gg_part + (int64_t)slot * ngg + bb);
+        for (int bb = 0; bb < ngg; ++bb)
+            gs += __ldcg(a.sb.gg_part + (int64_t)slot * a.sb.gg_stride + bb);
         double mu = qs > 0.0 ? sd.beta * gs / qs : 0.0;
         a.sb.mu[slot] = mu;
         unsigned long long nzs = atomicExch(a.sb.nnz_slot + slot, 0ull);
@@ -166,146 +205,177 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
 // ---------------------------------------------------------------------------
 // backprojection
 // ---------------------------------------------------------------------------
-struct BPArgs {
+// Ray table of a launch: every ray of every slot, set up once.
+struct TableArgs {
     DevGeom G;
     int first;
-    int nsb;
     const float* r;
-    float* gout;       // tile-local scratch (mode 0) or row-major volume (mode 1)
-    int mode;
-    int accumulate;
+    RayRec* table;       // [slot][ray slot]
     int64_t slot_stride;
-    double* gg_part;   // [slot][nsb * C] or null
 };
 
 template <int DIM>
+__device__ __forceinline__ void ray_table_body(const TableArgs& a, const WorkItem* items,
+                                               const StepDesc& sd, int slot) {
+    const DevGeom& G = a.G;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= sd.n_rays) return;
+    int w = find_item(items, sd.w0, sd.w1, k);
+    const WorkItem it = items[w];
+    int64_t within = k - it.ray_off;
+    int wu = it.u1 - it.u0;
+    int ku = it.u0 + (int)(within % wu);
+    int kv = it.v0 + (int)(within / wu);
+    const DevView V = G.views[it.view];
+    const DevVT E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
+    float q[3], d[3];
+    ray_setup(G, V, E, ku, kv, q, d);
+    RayRec rec;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        rec.q[c] = q[c];
+        rec.inv[c] = d[c] != 0.f ? 1.0f / d[c] : INFINITY;
+    }
+    rec.r = __ldg(a.r + ray_index(G, it.view, ku, kv));
+    rec.pad = 0.f;
+    a.table[(int64_t)slot * a.slot_stride + k] = rec;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_ray_table_inline(const TableArgs a,
+                                                          const __grid_constant__ InlineItems it) {
+    ray_table_body<DIM>(a, it.items, it.step, 0);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_ray_table_solver(const TableArgs a,
+                                                          const WorkItem* __restrict__ items,
+                                                          const StepDesc* __restrict__ steps) {
+    const StepDesc sd = steps[a.first + blockIdx.y];
+    ray_table_body<DIM>(a, items, sd, blockIdx.y);
+}
+
+struct BPArgs {
+    DevGeom G;
+    int first;
+    const RayRec* table;   // [slot][ray slot]
+    int64_t table_stride;
+    float* gout;           // tile-local scratch (mode 0) or row-major volume (mode 1)
+    int mode;
+    int accumulate;
+    int64_t slot_stride;
+    double* gg_part;       // [slot][voxel blocks] or null
+    int gg_stride;
+};
+
+// g_J = (A_I^J)^T r_I, voxel-driven: a thread owns one voxel of the tile and,
+// for every view of its chunk, sums len * r over the rays whose bins lie within
+// the voxel's shadow (half-width hw around the bin of the voxel's centre).  The
+// length is the voxel's slab clip of the ray, t = (plane - q) / d on each face,
+// i.e. the very crossings the forward walk evaluates, so forward and adjoint use
+// the same lengths.  No atomics: the C CTAs of a cluster (one per view chunk)
+// add their partial sums through distributed shared memory in a fixed order.
+template <int DIM>
 __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem* items,
-                                                 const StepDesc& sd, float* acc) {
+                                                 const StepDesc& sd, int slot) {
+    __shared__ float part[kBPThreads];
+    __shared__ double sh[kBPThreads / 32];
     cg::cluster_group cluster = cg::this_cluster();
     const DevGeom& G = a.G;
     const int C = (int)cluster.num_blocks();
-    const int rank = (int)cluster.block_rank();
-    const int slot = blockIdx.z;
-    const int sb = blockIdx.y;
+    const int chunk = (int)cluster.block_rank();
     const DevTile t = G.tiles[sd.j];
-    // sub-box: cut along the last axis
-    const int ax = DIM - 1;
-    const int W = t.n[ax];
-    const int s0 = (int)(((int64_t)sb * W) / a.nsb);
-    const int s1 = (int)(((int64_t)(sb + 1) * W) / a.nsb);
-    Box b;
+    const int nvox = t.n[0] * t.n[1] * t.n[2];
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = v < nvox;
+    const int x0 = valid ? v % t.n[0] : 0;
+    const int rest = valid ? v / t.n[0] : 0;
+    const int x1 = rest % t.n[1];
+    const int x2 = rest / t.n[1];
+    // voxel box in tile-centred coordinates
+    float lo[3], P[3];
+    lo[0] = -0.5f * (float)t.n[0] + (float)x0;
+    lo[1] = -0.5f * (float)t.n[1] + (float)x1;
+    lo[2] = DIM == 3 ? -0.5f * (float)t.n[2] + (float)x2 : -0.5f;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        b.lo[c] = c < DIM ? -0.5f * (float)t.n[c] : -0.5f;
-        b.n[c] = c < DIM ? t.n[c] : 1;
-    }
-    b.lo[ax] += (float)s0;
-    b.n[ax] = s1 - s0;
-    b.stride[0] = 1;
-    b.stride[1] = b.n[0];
-    b.stride[2] = b.n[0] * b.n[1];
-    b.base = 0;
-    const int nvox = b.n[0] * b.n[1] * b.n[2];
-    for (int v = threadIdx.x; v < nvox; v += blockDim.x) acc[v] = 0.f;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const float* __restrict__ r = a.r;
-    for (int w = sd.w0 + rank; w < sd.w1; w += C) {
-        const WorkItem it = items[w];
-        const DevView V = G.views[it.view];
-        const DevVT E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
-        // bins whose lines can meet this sub-box: project its corners (lanes 0..7)
-        float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
-        if (lane < (1 << DIM)) {
-            float P[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float off = c < DIM ? (((lane >> c) & 1) ? b.lo[c] + (float)b.n[c] : b.lo[c]) : 0.f;
-                P[c] = t.T[c] + off;
-            }
+    for (int c = 0; c < 3; ++c) P[c] = c < DIM ? t.T[c] + lo[c] + 0.5f : 0.f;
+    const RayRec* __restrict__ tab = a.table + (int64_t)slot * a.table_stride;
+    Kahan acc;
+    if (valid) {
+        for (int w = sd.w0 + chunk; w < sd.w1; w += C) {
+            const WorkItem it = items[w];
+            const DevView V = G.views[it.view];
+            const DevVT& E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
             float wu, wv;
             detector_coord(G, V, P, &wu, &wv);
-            umin = umax = wu;
-            vmin = vmax = wv;
-        }
+            const float hu = E.hw_u;
+            int ku0 = max(it.u0, (int)ceilf(wu - 0.5f - hu));
+            int ku1 = min(it.u1 - 1, (int)floorf(wu - 0.5f + hu));
+            int kv0 = it.v0, kv1 = it.v1 - 1;
+            if (DIM == 3) {
+                const float hv = E.hw_v;
+                kv0 = max(it.v0, (int)ceilf(wv - 0.5f - hv));
+                kv1 = min(it.v1 - 1, (int)floorf(wv - 0.5f + hv));
+            }
+            const int wdt = it.u1 - it.u0;
+            for (int kv = kv0; kv <= kv1; ++kv) {
+                const int64_t rowoff = it.ray_off + (int64_t)(kv - it.v0) * wdt - it.u0;
+                for (int ku = ku0; ku <= ku1; ++ku) {
+                    const RayRec rec = tab[rowoff + ku];
+                    float tin = -INFINITY, tout = INFINITY;
+                    bool hit = true;
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
-            umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, o));
-            umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
-            vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
-            vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-        }
-        umin = __shfl_sync(0xffffffffu, umin, 0);
-        umax = __shfl_sync(0xffffffffu, umax, 0);
-        vmin = __shfl_sync(0xffffffffu, vmin, 0);
-        vmax = __shfl_sync(0xffffffffu, vmax, 0);
-        int u0 = max(it.u0, (int)ceilf(umin - 0.5f) - 1);
-        int u1 = min(it.u1, (int)floorf(umax - 0.5f) + 2);
-        int v0 = it.v0, v1 = it.v1;
-        if (DIM == 3) {
-            v0 = max(it.v0, (int)ceilf(vmin - 0.5f) - 1);
-            v1 = min(it.v1, (int)floorf(vmax - 0.5f) + 2);
-        }
-        if (u1 <= u0 || v1 <= v0) continue;
-        const int wu = u1 - u0;
-        const int nr = wu * (v1 - v0);
-        for (int k = threadIdx.x; k < nr; k += blockDim.x) {
-            int ku = u0 + k % wu;
-            int kv = v0 + k / wu;
-            float rv = __ldg(r + ray_index(G, it.view, ku, kv));
-            if (rv == 0.f) continue;
-            float q[3], d[3];
-            ray_setup(G, V, E, ku, kv, q, d);
-            traverse<DIM>(q, d, b, [&](int idx, float len) {
-                if (len > 0.f) atomicAdd(acc + idx, len * rv);
-            });
+                    for (int c = 0; c < DIM; ++c) {
+                        if (isfinite(rec.inv[c])) {
+                            float ta = (lo[c] - rec.q[c]) * rec.inv[c];
+                            float tb = (lo[c] + 1.0f - rec.q[c]) * rec.inv[c];
+                            tin = fmaxf(tin, fminf(ta, tb));
+                            tout = fminf(tout, fmaxf(ta, tb));
+                        } else {
+                            hit = hit && rec.q[c] >= lo[c] && rec.q[c] < lo[c] + 1.0f;
+                        }
+                    }
+                    float len = hit ? fmaxf(tout - tin, 0.f) : 0.f;
+                    acc.add(len * rec.r);
+                }
+            }
         }
     }
+    part[threadIdx.x] = acc.s - acc.c;
     cluster.sync();
-    // each CTA of the cluster reduces one slice of the sub-box over all ranks
-    const int v_lo = (int)(((int64_t)rank * nvox) / C);
-    const int v_hi = (int)(((int64_t)(rank + 1) * nvox) / C);
     double gg = 0.0;
-    for (int v = v_lo + threadIdx.x; v < v_hi; v += blockDim.x) {
+    if (chunk == 0) {
         float s = 0.f;
-        for (int rr = 0; rr < C; ++rr) s += cluster.map_shared_rank(acc, rr)[v];
+        for (int rr = 0; rr < C; ++rr) s += cluster.map_shared_rank(part, rr)[threadIdx.x];
         s *= G.h;
-        int x0 = v % b.n[0];
-        int rest = v / b.n[0];
-        int x1 = rest % b.n[1];
-        int x2 = rest / b.n[1];
-        if (ax == 1) x1 += s0; else x2 += s0;
-        if (a.mode == 0) {
-            int64_t li = ((int64_t)x2 * t.n[1] + x1) * t.n[0] + x0;
-            a.gout[(int64_t)slot * a.slot_stride + li] = s;
-        } else {
-            int64_t gi = ((int64_t)(t.lo[2] + x2) * G.ny + (t.lo[1] + x1)) * G.nx + t.lo[0] + x0;
-            a.gout[gi] = a.accumulate ? a.gout[gi] + s : s;
+        if (valid) {
+            if (a.mode == 0) {
+                a.gout[(int64_t)slot * a.slot_stride + v] = s;
+            } else {
+                int64_t gi = ((int64_t)(t.lo[2] + x2) * G.ny + (t.lo[1] + x1)) * G.nx + t.lo[0] + x0;
+                a.gout[gi] = a.accumulate ? a.gout[gi] + s : s;
+            }
+            gg = (double)s * (double)s;
         }
-        gg += (double)s * (double)s;
-    }
-    if (a.gg_part) {
-        __shared__ double sh[kBPThreads / 32];
-        double bg = block_sum(gg, sh);
-        if (threadIdx.x == 0)
-            a.gg_part[((int64_t)slot * a.nsb + sb) * C + rank] = bg;
     }
     cluster.sync();
+    if (a.gg_part && chunk == 0) {
+        double bg = block_sum(gg, sh);
+        if (threadIdx.x == 0) a.gg_part[(int64_t)slot * a.gg_stride + blockIdx.x] = bg;
+    }
 }
 
 template <int DIM>
 __global__ void __launch_bounds__(kBPThreads) k_backproject_inline(
     const BPArgs a, const __grid_constant__ InlineItems it) {
-    extern __shared__ float acc[];
-    backproject_body<DIM>(a, it.items, it.step, acc);
+    backproject_body<DIM>(a, it.items, it.step, 0);
 }
 
 template <int DIM>
 __global__ void __launch_bounds__(kBPThreads) k_backproject_solver(
     const BPArgs a, const WorkItem* __restrict__ items, const StepDesc* __restrict__ steps) {
-    extern __shared__ float acc[];
     const StepDesc sd = steps[a.first + blockIdx.z];
-    backproject_body<DIM>(a, items, sd, acc);
+    backproject_body<DIM>(a, items, sd, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -412,10 +482,6 @@ __global__ void k_sq_residual(const float* y, const float* ax, int64_t n, double
     if (threadIdx.x == 0) out[blockIdx.x] = b;
 }
 
-template <class K>
-void set_smem(K kernel, int bytes) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
 
 }  // namespace
 
@@ -423,20 +489,16 @@ void set_smem(K kernel, int bytes) {
 // host launchers
 // ---------------------------------------------------------------------------
 BPPlan plan_backprojection(const DevGeom& G, const DevTile& tile, int nslots, int sm_count) {
+    // One thread per voxel; when a batch has fewer than ~2048 threads per SM the
+    // views of a slot are split into C chunks (one cluster of C CTAs per voxel
+    // block).
     BPPlan p;
-    const int ax = G.dim - 1;
     const int64_t nv = (int64_t)tile.n[0] * tile.n[1] * tile.n[2];
-    const int64_t slab = nv / tile.n[ax];  // voxels per unit thickness along ax
-    int nsb = (int)((nv + kMaxSubboxFloats - 1) / kMaxSubboxFloats);
-    p.C = 8;
-    // enough CTAs for about two waves, but sub-boxes of at least 4096 voxels
-    int64_t want = (int64_t)2 * sm_count;
-    while ((int64_t)nsb * p.C * nslots < want && nv / (nsb + 1) >= 4096 && nsb < tile.n[ax])
-        ++nsb;
-    if (nsb > tile.n[ax]) nsb = tile.n[ax];
-    p.nsb = nsb;
-    int64_t thick = (tile.n[ax] + nsb - 1) / nsb;
-    p.smem_bytes = (int)(thick * slab * sizeof(float));
+    p.blocks = (int)((nv + kBPThreads - 1) / kBPThreads);
+    int64_t threads = (int64_t)p.blocks * kBPThreads * nslots;
+    int64_t want = (int64_t)2048 * sm_count;
+    int C = (int)((want + threads - 1) / threads);
+    p.C = std::max(1, std::min(8, C));
     return p;
 }
 
@@ -444,59 +506,91 @@ static cudaError_t launch_bp_common(const DevGeom& G, const BPPlan& plan, int ns
                                     cudaStream_t s, const BPArgs& a, const InlineItems* inl,
                                     const WorkItem* items, const StepDesc* steps) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(plan.C, plan.nsb, nslots);
+    cfg.gridDim = dim3(plan.blocks, plan.C, nslots);
     cfg.blockDim = dim3(kBPThreads);
-    cfg.dynamicSmemBytes = plan.smem_bytes;
+    cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = plan.C;
-    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = plan.C;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (inl) {
-        if (G.dim == 2) {
-            set_smem(k_backproject_inline<2>, plan.smem_bytes);
-            return cudaLaunchKernelEx(&cfg, k_backproject_inline<2>, a, *inl);
-        }
-        set_smem(k_backproject_inline<3>, plan.smem_bytes);
+        if (G.dim == 2) return cudaLaunchKernelEx(&cfg, k_backproject_inline<2>, a, *inl);
         return cudaLaunchKernelEx(&cfg, k_backproject_inline<3>, a, *inl);
     }
-    if (G.dim == 2) {
-        set_smem(k_backproject_solver<2>, plan.smem_bytes);
-        return cudaLaunchKernelEx(&cfg, k_backproject_solver<2>, a, items, steps);
-    }
-    set_smem(k_backproject_solver<3>, plan.smem_bytes);
+    if (G.dim == 2) return cudaLaunchKernelEx(&cfg, k_backproject_solver<2>, a, items, steps);
     return cudaLaunchKernelEx(&cfg, k_backproject_solver<3>, a, items, steps);
 }
 
+static cudaError_t launch_table(const DevGeom& G, int nslots, int64_t max_rays, cudaStream_t s,
+                                const TableArgs& t, const InlineItems* inl, const WorkItem* items,
+                                const StepDesc* steps) {
+    if (max_rays <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((max_rays + 255) / 256), nslots);
+    if (inl) {
+        if (G.dim == 2) k_ray_table_inline<2><<<grid, 256, 0, s>>>(t, *inl);
+        else k_ray_table_inline<3><<<grid, 256, 0, s>>>(t, *inl);
+    } else {
+        if (G.dim == 2) k_ray_table_solver<2><<<grid, 256, 0, s>>>(t, items, steps);
+        else k_ray_table_solver<3><<<grid, 256, 0, s>>>(t, items, steps);
+    }
+    return cudaGetLastError();
+}
+
+// Lanes per ray: enough threads for ~2048 per SM when rays are few.
+int lanes_per_ray(int64_t rays, int sm_count) {
+    int64_t want = (int64_t)2048 * sm_count;
+    if (rays * 2 > want) return 1;
+    if (rays * 4 > want) return 2;
+    return 4;
+}
+
+template <int DIM>
+static void project_inline_L(int L, dim3 grid, const DevGeom& G, const InlineItems& it,
+                             const float* x, float* out, int accumulate, cudaStream_t s) {
+    if (L == 1) k_project_inline<DIM, 1><<<grid, kFwdThreads, 0, s>>>(G, it, x, out, accumulate);
+    else if (L == 2) k_project_inline<DIM, 2><<<grid, kFwdThreads, 0, s>>>(G, it, x, out, accumulate);
+    else k_project_inline<DIM, 4><<<grid, kFwdThreads, 0, s>>>(G, it, x, out, accumulate);
+}
+
 cudaError_t launch_project_inline(const DevGeom& G, const InlineItems& it, const float* x,
-                                  float* out, int accumulate, cudaStream_t s) {
+                                  float* out, int accumulate, int sm_count, cudaStream_t s) {
     if (it.step.n_rays <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((it.step.n_rays + kFwdThreads - 1) / kFwdThreads));
-    if (G.dim == 2)
-        k_project_inline<2><<<grid, kFwdThreads, 0, s>>>(G, it, x, out, accumulate);
-    else
-        k_project_inline<3><<<grid, kFwdThreads, 0, s>>>(G, it, x, out, accumulate);
+    int L = lanes_per_ray(it.step.n_rays, sm_count);
+    dim3 grid((unsigned)((it.step.n_rays * L + kFwdThreads - 1) / kFwdThreads));
+    if (G.dim == 2) project_inline_L<2>(L, grid, G, it, x, out, accumulate, s);
+    else project_inline_L<3>(L, grid, G, it, x, out, accumulate, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_backproject_inline(const DevGeom& G, const DevTile& tile,
                                       const InlineItems& it, const float* r, float* g,
-                                      int accumulate, int sm_count, cudaStream_t s) {
+                                      int accumulate, RayRec* table, int sm_count,
+                                      cudaStream_t s) {
+    TableArgs ta;
+    ta.G = G;
+    ta.first = 0;
+    ta.r = r;
+    ta.table = table;
+    ta.slot_stride = 0;
+    cudaError_t e = launch_table(G, 1, it.step.n_rays, s, ta, &it, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
     BPPlan plan = plan_backprojection(G, tile, 1, sm_count);
     BPArgs a;
     a.G = G;
     a.first = 0;
-    a.nsb = plan.nsb;
-    a.r = r;
+    a.table = table;
+    a.table_stride = 0;
     a.gout = g;
     a.mode = 1;
     a.accumulate = accumulate;
     a.slot_stride = 0;
     a.gg_part = nullptr;
-    cudaError_t e = launch_bp_common(G, plan, 1, s, a, &it, nullptr, nullptr);
+    a.gg_stride = 0;
+    e = launch_bp_common(G, plan, 1, s, a, &it, nullptr, nullptr);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -506,18 +600,28 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
                          int sm_count, cudaStream_t s, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], s);
     BPPlan plan = plan_backprojection(G, tile, b.nslots, sm_count);
-    // 1. g_J = (A_I^J)^T r_I per slot
+    // 1. g_J = (A_I^J)^T r_I per slot: ray table, then voxel-driven sums
+    TableArgs ta;
+    ta.G = G;
+    ta.first = b.first;
+    ta.r = sb.r;
+    ta.table = sb.table;
+    ta.slot_stride = sb.table_stride;
+    cudaError_t e = launch_table(G, b.nslots, b.max_rays, s, ta, nullptr, items, steps);
+    if (e != cudaSuccess) return e;
+    if (plan.blocks > sb.gg_stride) return cudaErrorInvalidValue;
     BPArgs a;
     a.G = G;
     a.first = b.first;
-    a.nsb = plan.nsb;
-    a.r = sb.r;
+    a.table = sb.table;
+    a.table_stride = sb.table_stride;
     a.gout = sb.g;
     a.mode = 0;
     a.accumulate = 0;
     a.slot_stride = sb.g_stride;
     a.gg_part = sb.gg_part;
-    cudaError_t e = launch_bp_common(G, plan, b.nslots, s, a, nullptr, items, steps);
+    a.gg_stride = sb.gg_stride;
+    e = launch_bp_common(G, plan, b.nslots, s, a, nullptr, items, steps);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
     // 2. p = A x_J, q = A g_J, ||q||^2, mu
@@ -527,14 +631,22 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     f.steps = steps;
     f.first = b.first;
     f.sync_epoch = b.sync_epoch;
-    f.n_gg = plan.nsb * plan.C;
+    f.n_gg = plan.blocks;
     f.sb = sb;
-    int64_t nb = (b.max_rays + kFwdThreads - 1) / kFwdThreads;
+    const int L = lanes_per_ray(b.max_rays * b.nslots, sm_count);
+    int64_t nb = (b.max_rays * L + kFwdThreads - 1) / kFwdThreads;
     if (nb < 1) nb = 1;
     if (nb > sb.max_fwd_blocks) return cudaErrorInvalidValue;
     dim3 grid((unsigned)nb, b.nslots);
-    if (G.dim == 2) k_forward_dual<2><<<grid, kFwdThreads, 0, s>>>(f);
-    else k_forward_dual<3><<<grid, kFwdThreads, 0, s>>>(f);
+    if (G.dim == 2) {
+        if (L == 1) k_forward_dual<2, 1><<<grid, kFwdThreads, 0, s>>>(f);
+        else if (L == 2) k_forward_dual<2, 2><<<grid, kFwdThreads, 0, s>>>(f);
+        else k_forward_dual<2, 4><<<grid, kFwdThreads, 0, s>>>(f);
+    } else {
+        if (L == 1) k_forward_dual<3, 1><<<grid, kFwdThreads, 0, s>>>(f);
+        else if (L == 2) k_forward_dual<3, 2><<<grid, kFwdThreads, 0, s>>>(f);
+        else k_forward_dual<3, 4><<<grid, kFwdThreads, 0, s>>>(f);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], s);

