@@ -160,7 +160,7 @@ enum { CSGD_SYNC_COLUMN = 0, CSGD_SYNC_EPOCH = 1 };
 
 typedef struct {
     int32_t sampling;      /* CSGD_SAMPLE_*: Alg. 2 order, uniform, Alg. 3
-                              importance, Sec. III-E mixed                        */
+                              importance, Sec. III-D mixed                        */
     int32_t sync;          /* CSGD_SYNC_COLUMN: refresh r after each column block
                               (Alg. 2-4 as printed); CSGD_SYNC_EPOCH: one refresh
                               per epoch (Sec. II-F parameter-server reading)       */

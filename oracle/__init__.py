@@ -13,7 +13,7 @@ Modules, each following the paper's definitions in plain FP64:
 ``siddon``    A_i^j = length of ray i inside voxel j, by the alpha-merge (Sec. II-A)
 ``blocks``    row blocks I, column blocks J and the operators A_I^J, (A_I^J)^T (Eq. e1)
 ``ptable``    the importance table P(I,J) = P_S / P_T (Sec. II-C, Alg. 3)
-``schedule``  the random choice of (I, J) blocks and groups (Alg. 3, Alg. 4, Sec. III-E)
+``schedule``  the random choice of (I, J) blocks and groups (Alg. 3, Alg. 4, Sec. III-D)
 ``solver``    Alg. 1 (basic iteration) inside Alg. 2 / 3 / 4
 ``metrics``   SNR, observation gap, RMSE (Sec. III)
 

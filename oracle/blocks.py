@@ -141,7 +141,7 @@ def project_block(part: Partition, row_blocks, j: int, x: np.ndarray):
 
 
 def backproject_block(part: Partition, row_blocks, j: int, r_rows: np.ndarray):
-    """g_J = (A_I^J)^T r_I (Eq. 'direction', Alg. 1 first line), FP64.
+    """g_J = (A_I^J)^T r_I (Eq. 'direction', Alg. 1), FP64.
 
     ``r_rows`` holds r on the sorted rows of the union of ``row_blocks``.
     Returns a full-size volume that is zero outside tile j.

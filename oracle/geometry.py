@@ -5,7 +5,7 @@ Test infrastructure only (see the package docstring).
 The paper fixes the model y = Ax + e with A_i^j the length of ray i inside voxel
 j (Sec. II-A), a point source whose detector is perpendicular to the line from
 the source to the detector centre (Sec. II-D), a circular 2D fan trajectory
-(Sec. III) and an arbitrary 3D trajectory (Sec. III-F).  It leaves the angle
+(Sec. III) and an arbitrary 3D trajectory (Sec. III-E).  It leaves the angle
 origin, the rotation sense and the bin centring open; the readings used here
 (and by every other part of this repository) are:
 

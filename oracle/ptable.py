@@ -12,7 +12,7 @@ area of J on the whole detector over the whole trajectory.  The readings used:
 * areas are measured in detector-bin units (bin k covers [k, k+1));
 * a row block I with several views sums the per-view overlaps, so a group
   I_g = union of row blocks has P_S(I_g, J) = sum of the members' P_S and
-  beta = b * P_S(I_g, J) / P_T(J) grows with the group, as Sec. III-C notes;
+  beta = b * P_S(I_g, J) / P_T(J) grows with the group, as Sec. III-B notes;
 * P_T(J) = 0 (a tile no ray sees) gives P(., J) = 0;
 * an overlap below 1e-9 bin units counts as none: a shadow edge that falls
   exactly on a sub-area boundary otherwise leaves a rounding sliver whose sign

@@ -18,7 +18,7 @@ published definition, the same generator and the same way of consuming it:
   weights).  Drawing stops early when no block with positive weight is left;
   a partly filled last group is kept.
 * Weights: importance w = P(I, J) (Alg. 3, Alg. 4); uniform w = 1 (the equal
-  probability choice of Sec. II-C); mixed (Sec. III-E)
+  probability choice of Sec. II-C); mixed (Sec. III-D)
   w = P + theta_e (P_max - P) where P_max is the largest P(., J) among the row
   blocks that share the views of I, theta_e = min(1, e * theta_step) in epoch e
   (counted from 0; the paper raises theta by 1/40 per epoch); sequential

@@ -17,7 +17,7 @@ x_J itself stays fixed during an epoch; after the row draws of one column block
 the residual is refreshed on the rows It that were drawn, r_It = y_It -
 sum_j z_It^j (Alg. 2-4; the It restriction is the remark after Alg. 3).  At the
 end of the epoch every updated block becomes the mean of its candidates,
-x_J = x^_J / count_J, and x^ and the counts are reset (Alg. 2-4 last line).
+x_J = x^_J / count_J, and x^ and the counts are reset (end of the epoch loop of Alg. 2-4).
 
 Readings where the paper is silent:
 

@@ -1,4 +1,4 @@
-// Random block choice of Alg. 3 / Alg. 4 and the mixed weights of Sec. III-E.
+// Random block choice of Alg. 3 / Alg. 4 and the mixed weights of Sec. III-D.
 //
 // The paper does not name a generator.  The rules below are fixed so that any
 // implementation of them (this one, or an independent one used as a check)

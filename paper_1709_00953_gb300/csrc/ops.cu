@@ -2,7 +2,7 @@
 //
 //   k_forward      z_I = A_I^J x_J (one vector) or, in the solver, p = A x_J and
 //                  q = A g_J in one traversal with ||q||^2 in FP64 and the step
-//                  length mu computed by the last CTA (Alg. 1 lines 2-3).
+//                  length mu computed by the last CTA (Alg. 1, Eq. 'step').
 //   k_backproject  g_J = (A_I^J)^T r_I (Eq. 'direction'): ray-driven traversal of a
 //                  shared-memory sub-box of the tile, partial sums reduced across
 //                  the CTAs of a thread-block cluster through distributed shared

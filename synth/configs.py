@@ -12,7 +12,7 @@ A workload is a plain dict:
 
 Seeds: data seed 1709 + c, schedule seed 0x17090953 + c for configuration c.
 The sizes follow the paper's simulations (Sec. III: 2D fan with 360 views,
-2 x 2 volume blocks and 2 detector sub-areas; Sec. III-F: a 3D cone scan with
+2 x 2 volume blocks and 2 detector sub-areas; Sec. III-E: a 3D cone scan with
 720 views and group size 90) scaled to the three workloads below.
 """
 from __future__ import annotations
@@ -124,7 +124,7 @@ def small_cone3d(n=24, views=24, nd=40, tiles=(2, 2, 3), group=4, steps=24, du=1
 
 
 def random_sphere_poses(n_views: int, radius: float, sdd: float, seed: int) -> np.ndarray:
-    """Sec. III-F trajectory: source at radius r with random polar / azimuth angles,
+    """Sec. III-E trajectory: source at radius r with random polar / azimuth angles,
     detector perpendicular to the source-centre line at distance sdd from the source.
     Returns (n_views, 12) = S, C, e_u, e_v."""
     rng = np.random.Generator(np.random.PCG64(seed))

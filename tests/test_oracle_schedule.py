@@ -1,4 +1,4 @@
-"""Pins of the oracle's block choice (Alg. 3 / Alg. 4 sampling, Sec. III-E mixed)."""
+"""Pins of the oracle's block choice (Alg. 3 / Alg. 4 sampling, Sec. III-D mixed)."""
 import math
 import os
 
@@ -95,7 +95,7 @@ def test_gamma_takes_a_prefix_and_sequential_order():
 
 
 def test_mixed_weights_ramp():
-    """Sec. III-E: w = P + theta (P_max - P) within one projection; theta reaches 1 after
+    """Sec. III-D: w = P + theta (P_max - P) within one projection; theta reaches 1 after
     40 epochs at the paper's step of 1/40, where all sub-areas of a view are equal."""
     P = np.array([[0.1], [0.3], [0.2], [0.4]])
     vb = [0, 0, 1, 1]
