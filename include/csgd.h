@@ -147,6 +147,32 @@ int32_t csgd_backproject_block(const csgd_partition* part, const int32_t* row_bl
                                int32_t n_rb, int32_t j, const float* r, float* g,
                                int32_t accumulate, csgd_stream stream);
 
+/* Backprojection that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory while they
+ * run, such as a pre-planned real-time loop that must not call cudaMalloc or an
+ * embedding whose memory is all handed out at start-up.  It computes the same g
+ * as csgd_backproject_block (same kernels, same arguments and layouts), but its
+ * scratch ray table is a fixed array of CSGD_NOALLOC_MAX_RAYS records (32 bytes
+ * each, 8 MiB) in the library's global memory, held by every GPU that loads the
+ * library until the process exits; it calls no cudaMalloc, cudaFree or other
+ * allocating routine, host or device, when it succeeds.
+ * Requirements and limits:
+ *  - the rays of the call (views of the row blocks x bins of the tile's shadow
+ *    in their sub-areas) must number at most CSGD_NOALLOC_MAX_RAYS; otherwise
+ *    CSGD_ERR_INVALID_ARG is returned and nothing is launched;
+ *  - the partition's tables must already be on the device: make one ordinary
+ *    device call with it first (for example csgd_project_block), otherwise
+ *    CSGD_ERR_STATE is returned;
+ *  - the first call on a device looks up the array's device address with that
+ *    device current; make that first call before any stream capture;
+ *  - all calls share the array and it keeps the last call's contents: calls
+ *    that overlap on the GPU (other streams, other host threads) race on it and
+ *    must be serialised by the caller. */
+#define CSGD_NOALLOC_MAX_RAYS 262144
+int32_t csgd_backproject_block_noalloc(const csgd_partition* part, const int32_t* row_blocks,
+                                       int32_t n_rb, int32_t j, const float* r, float* g,
+                                       int32_t accumulate, csgd_stream stream);
+
 /* out = A x over all rows and all tiles (device pointers). */
 int32_t csgd_project_full(const csgd_partition* part, const float* x, float* out,
                           csgd_stream stream);

@@ -96,6 +96,8 @@ SIGNATURES = {
     "csgd_project_block": ([_vp, ctypes.POINTER(_i32), _i32, _i32, _vp, _vp, _i32, _vp], _i32),
     "csgd_backproject_block": ([_vp, ctypes.POINTER(_i32), _i32, _i32, _vp, _vp, _i32, _vp], _i32),
     "csgd_project_full": ([_vp, _vp, _vp, _vp], _i32),
+    "csgd_backproject_block_noalloc": ([_vp, ctypes.POINTER(_i32), _i32, _i32, _vp, _vp, _i32, _vp],
+                                       _i32),
     "csgd_schedule_generate": ([_vp, ctypes.POINTER(SolverParams), _i32, ctypes.POINTER(_i32),
                                 _i64, ctypes.POINTER(_i64)], _i32),
     "csgd_solver_footprint_bytes": ([_vp, ctypes.POINTER(SolverParams), ctypes.POINTER(_i64)], _i32),
@@ -281,6 +283,27 @@ def backproject_block(part: Partition, row_blocks, j: int, r, g, accumulate=Fals
                                          _dev_ptr(r, "r", part.n_rays),
                                          _dev_ptr(g, "g", part.n_voxels), int(bool(accumulate)),
                                          _stream(stream)))
+
+
+NOALLOC_MAX_RAYS = 262144  # CSGD_NOALLOC_MAX_RAYS of include/csgd.h
+
+
+def backproject_block_noalloc(part: Partition, row_blocks, j: int, r, g, accumulate=False,
+                              stream=None):
+    """Same as backproject_block, for callers that cannot allocate device memory.
+
+    The library keeps this call's scratch in a fixed 8 MiB array on the GPU
+    instead of allocating it, so it works where cudaMalloc is not allowed (after
+    start-up in a real-time loop, or when all device memory is handed out in
+    advance).  At most NOALLOC_MAX_RAYS rays per call; one ordinary device call
+    with the partition must come first (it uploads the partition's tables);
+    concurrent calls share the array and must not overlap on the GPU.
+    """
+    arr, ptr = _rows(row_blocks)
+    _check(load().csgd_backproject_block_noalloc(part.handle, ptr, arr.shape[0], int(j),
+                                                 _dev_ptr(r, "r", part.n_rays),
+                                                 _dev_ptr(g, "g", part.n_voxels),
+                                                 int(bool(accumulate)), _stream(stream)))
 
 
 def project_full(part: Partition, x, out, stream=None):

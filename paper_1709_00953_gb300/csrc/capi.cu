@@ -597,6 +597,101 @@ int32_t csgd_backproject_block(const csgd_partition* Pc, const int32_t* row_bloc
     return run_inline(P, items, j, false, r, g, accumulate, (cudaStream_t)stream);
 }
 
+int32_t csgd_backproject_block_noalloc(const csgd_partition* Pc, const int32_t* row_blocks,
+                                       int32_t n_rb, int32_t j, const float* r, float* g,
+                                       int32_t accumulate, csgd_stream stream) {
+    // Same result as csgd_backproject_block, with the ray table in the fixed
+    // array of ops.cu and every other piece of state on the stack: no host or
+    // device allocation on success.
+    csgd_partition* P = const_cast<csgd_partition*>(Pc);
+    if (!P || !r || !g || !row_blocks) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    const Partition& p = P->p;
+    if (j < 0 || j >= p.n) return fail(CSGD_ERR_INVALID_ARG, "column block out of range");
+    if (n_rb < 1 || n_rb > p.m) return fail(CSGD_ERR_INVALID_ARG, "bad number of row blocks");
+    unsigned char seen[65536 / 8];
+    memset(seen, 0, sizeof(seen));
+    for (int k = 0; k < n_rb; ++k) {
+        int i = row_blocks[k];
+        if (i < 0 || i >= p.m) return fail(CSGD_ERR_INVALID_ARG, "row block out of range");
+        if (seen[i >> 3] & (1u << (i & 7))) return fail(CSGD_ERR_INVALID_ARG, "row blocks must be distinct");
+        seen[i >> 3] |= (unsigned char)(1u << (i & 7));
+    }
+    if (!P->on_device)
+        return fail(CSGD_ERR_STATE,
+                    "partition tables are not on the device yet: make one ordinary device call "
+                    "with this partition (e.g. csgd_project_block) before the allocation-free one");
+    int dev = 0;
+    CSGD_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != p.device) return fail(CSGD_ERR_INVALID_ARG, "partition tables live on another device");
+    // count the rays first: reject the call before launching anything
+    int64_t total = 0;
+    for (int r2 = 0; r2 < n_rb; ++r2) {
+        int su0, su1, sv0, sv1;
+        p.subrect(row_blocks[r2], &su0, &su1, &sv0, &sv1);
+        for (int v : p.views_of(row_blocks[r2])) {
+            const DevVT& e = p.vt(v, j);
+            int u0 = std::max(su0, e.u0), u1 = std::min(su1, e.u1);
+            int v0 = std::max(sv0, e.v0), v1 = std::min(sv1, e.v1);
+            if (u1 > u0 && v1 > v0) total += (int64_t)(u1 - u0) * (v1 - v0);
+        }
+    }
+    if (total > CSGD_NOALLOC_MAX_RAYS)
+        return fail(CSGD_ERR_INVALID_ARG,
+                    "the call covers " + std::to_string(total) + " rays, more than "
+                    "CSGD_NOALLOC_MAX_RAYS = " + std::to_string(CSGD_NOALLOC_MAX_RAYS));
+    RayRec* table = nullptr;
+    CSGD_CUDA(noalloc_table_address(dev, &table), "cudaGetSymbolAddress(ray table)");
+    cudaStream_t s = (cudaStream_t)stream;
+    // Fill launches of at most kMaxInlineItems views on the stack, in the same
+    // order as csgd_backproject_block; later launches accumulate.
+    InlineItems it;
+    int cnt = 0;
+    int64_t rays = 0;
+    bool first = true;
+    auto flush = [&]() -> int {
+        it.step.j = j;
+        it.step.w0 = 0;
+        it.step.w1 = cnt;
+        it.step.n_rays = rays;
+        it.step.step = 0;
+        it.step.beta = 0.0;
+        it.step.pad = 0;
+        it.n = cnt;
+        cudaError_t e = launch_backproject_inline(p.dg, p.tiles_h[j], it, r, g,
+                                                  first ? accumulate : 1, table, P->sm_count, s);
+        if (e != cudaSuccess) return cuda_fail(e, "backproject kernel");
+        first = false;
+        cnt = 0;
+        rays = 0;
+        return CSGD_OK;
+    };
+    for (int r2 = 0; r2 < n_rb; ++r2) {
+        int su0, su1, sv0, sv1;
+        p.subrect(row_blocks[r2], &su0, &su1, &sv0, &sv1);
+        for (int v : p.views_of(row_blocks[r2])) {
+            const DevVT& e = p.vt(v, j);
+            int u0 = std::max(su0, e.u0), u1 = std::min(su1, e.u1);
+            int v0 = std::max(sv0, e.v0), v1 = std::min(sv1, e.v1);
+            if (u1 <= u0 || v1 <= v0) continue;
+            WorkItem& w = it.items[cnt++];
+            w.view = v;
+            w.slot = 0;
+            w.u0 = u0; w.u1 = u1; w.v0 = v0; w.v1 = v1;
+            w.ray_off = rays;
+            rays += (int64_t)(u1 - u0) * (v1 - v0);
+            if (cnt == kMaxInlineItems) {
+                int rc = flush();
+                if (rc) return rc;
+            }
+        }
+    }
+    if (cnt > 0 || first) {
+        int rc = flush();
+        if (rc) return rc;
+    }
+    return CSGD_OK;
+}
+
 int32_t csgd_project_full(const csgd_partition* Pc, const float* x, float* out,
                           csgd_stream stream) {
     csgd_partition* P = const_cast<csgd_partition*>(Pc);

@@ -15,6 +15,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "device.cuh"
 #include "ops.h"
@@ -593,6 +594,40 @@ cudaError_t launch_backproject_inline(const DevGeom& G, const DevTile& tile,
     e = launch_bp_common(G, plan, 1, s, a, &it, nullptr, nullptr);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Backprojection without allocation
+//
+// Callers that cannot allocate device memory at the time they run (code inside a
+// pre-planned real-time loop, a host that hands out all device memory up front,
+// an embedding that forbids cudaMalloc after start-up) use this variant.  Its
+// ray table lives in a fixed array in the module's global memory instead of a
+// per-call allocation: every GPU that loads the library holds the array until
+// the process exits.  All calls share it, so calls that overlap on the GPU (two
+// streams, or two host threads) race on it.  Each launch writes every record it
+// reads before reading it, so nothing needs clearing between calls.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) RayRec g_noalloc_table[kNoAllocMaxRays];
+
+namespace {
+std::mutex g_noalloc_mu;
+RayRec* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+cudaError_t noalloc_table_address(int device, RayRec** out) {
+    // Host code cannot use the array's name as a device address: look the
+    // address up once per device, with that device current (the caller's).
+    if (device < 0 || device >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_table);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[device] = (RayRec*)ptr;
+    }
+    *out = g_noalloc_ptr[device];
+    return cudaSuccess;
 }
 
 cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* items,

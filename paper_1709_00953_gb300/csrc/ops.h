@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "../../include/csgd.h"
 #include "common.h"
 
 namespace csgd {
@@ -38,6 +39,13 @@ cudaError_t launch_backproject_inline(const DevGeom& G, const DevTile& tile,
                                       const InlineItems& it, const float* r, float* g,
                                       int accumulate, RayRec* table, int sm_count,
                                       cudaStream_t s);
+
+// ---- backprojection without allocation (fixed ray table in global memory) --
+constexpr int kNoAllocMaxRays = CSGD_NOALLOC_MAX_RAYS;
+constexpr int kNoAllocMaxDevices = 64;
+// Device address of the fixed ray table, looked up once per device (the current
+// one) with cudaGetSymbolAddress.
+cudaError_t noalloc_table_address(int device, RayRec** out);
 
 // ---- solver operators (device item / step arrays, several slots) -----------
 struct SolverBuffers {
