@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
     const bool active = k < sd.n_rays;
     float pp = 0.f, qp = 0.f;
     long long nz = 0;
+    int first_idx = -1, last_idx = -2;
     int64_t ray = 0;
     if (active) {
         int w = find_item(a.items, sd.w0, sd.w1, k);
@@ -152,11 +153,20 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
             nz = walk<DIM>(q, d, b, t0, t1, [&](int idx, float len) {
                 ax.add(len * __ldg(xj + idx));
                 ag.add(len * __ldg(gj + idx));
+                if (len > 0.f) {
+                    if (first_idx < 0) first_idx = idx;
+                    last_idx = idx;
+                }
             });
             pp = ax.s - ax.c;
             qp = ag.s - ag.c;
         }
         ray = ray_index(G, it.view, ku, kv);
+    }
+    if (L > 1) {
+        // a voxel cut by the split between two lanes was counted by both
+        int prev_last = __shfl_up_sync(0xffffffffu, last_idx, 1);
+        if (sub > 0 && first_idx >= 0 && prev_last == first_idx) --nz;
     }
     float pv = G.h * lane_sum<L>(pp);
     float qv = G.h * lane_sum<L>(qp);
