@@ -64,6 +64,8 @@ struct DevGeom {
     int32_t n_tiles;
     float pu, pv;          // bin pitch in voxel units (radians for the curved arc)
     float cu, cv;          // (nu-1)/2, (nv-1)/2
+    float inv_pu, inv_pv;  // 1 / pu, 1 / pv
+    int32_t fast_arc;      // curved detector within |gamma| < 0.46 rad: series atan
     float h;               // voxel edge (world units): lengths are scaled by h
     const DevView* views;
     const DevVT* vt;       // [view][tile]
@@ -77,7 +79,7 @@ struct RayRec {
     float q[3];
     float r;
     float inv[3];
-    float pad;
+    int32_t ray;  // index of the ray in the sinogram (below 2^31)
 };
 
 // One step of the solver as the kernels see it.

@@ -57,7 +57,7 @@ int geometry_from_desc(const csgd_geometry_desc* d, Geometry* g, std::string* er
         *err = "detector bin counts must be in [1, 32768]";
         return CSGD_ERR_INVALID_ARG;
     }
-    if (g->n_rays() > ((int64_t)1 << 40)) {
+    if (g->n_rays() >= ((int64_t)1 << 31)) {
         *err = "too many rays";
         return CSGD_ERR_INVALID_ARG;
     }
@@ -528,6 +528,9 @@ int partition_build(const Geometry* gp, const csgd_partition_desc* d, Partition*
     dg.pv = (float)pv_v;
     dg.cu = (float)cu;
     dg.cv = (float)cv;
+    dg.inv_pu = (float)(1.0 / pu_v);
+    dg.fast_arc = (g.kind == CSGD_FAN_2D_CURVED && 0.5 * g.nu * pu_v + 2 * pu_v < 0.46) ? 1 : 0;
+    dg.inv_pv = (float)(1.0 / pv_v);
     dg.h = (float)g.h;
     return CSGD_OK;
 }

@@ -88,17 +88,18 @@ __device__ __forceinline__ void forward_single(const DevGeom& G, const WorkItem*
         int kv = it.v0 + (int)(within / wu);
         const DevView V = G.views[it.view];
         const DevVT E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
-        float q[3], d[3];
+        float q[3], d[3], inv[3];
         ray_setup(G, V, E, ku, kv, q, d);
+        reciprocal(d, inv);
         int base = (t.lo[2] * G.ny + t.lo[1]) * G.nx + t.lo[0];
         Box b = tile_box(t, DIM, base, G.nx, G.nx * G.ny);
         float tin, tout;
-        if (clip<DIM>(q, d, b, &tin, &tout)) {
+        if (clip<DIM>(q, inv, b, &tin, &tout)) {
             float dt = (tout - tin) * (1.0f / L);
             float t0 = sub == 0 ? tin : fmaf((float)sub, dt, tin);
             float t1 = sub == L - 1 ? tout : fmaf((float)(sub + 1), dt, tin);
             Kahan acc;
-            walk<DIM>(q, d, b, t0, t1, [&](int idx, float len) { acc.add(len * __ldg(x + idx)); });
+            walk<DIM>(q, inv, b, t0, t1, [&](int idx, float len) { acc.add(len * __ldg(x + idx)); });
             part = acc.s - acc.c;
         }
         ray = ray_index(G, it.view, ku, kv);
@@ -114,16 +115,20 @@ __global__ void __launch_bounds__(kFwdThreads) k_project_inline(
     forward_single<DIM, L>(G, it.items, it.step, x, out, accumulate);
 }
 
+// p = A x_J and q = A g_J for every ray of a slot in one walk (z = p + mu q by
+// linearity), with ||q||^2 in FP64.  Rays come from the batch's ray table (set
+// up once for the backprojection), split over L lanes by parameter range.  Each
+// warp writes its partial sums; the last warp of the slot to finish adds them
+// in a fixed order and computes mu = beta g^T g / q^T q (no grid barrier).
 template <int DIM, int L>
 __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArgs a) {
-    __shared__ double sh[kFwdThreads / 32];
-    __shared__ int last;
     const DevGeom& G = a.G;
     const int slot = blockIdx.y;
     const StepDesc sd = a.steps[a.first + slot];
     const DevTile t = G.tiles[sd.j];
     const float* __restrict__ xj = a.sb.x + t.voff;
     const float* __restrict__ gj = a.sb.g + (int64_t)slot * a.sb.g_stride;
+    const int lane = threadIdx.x & 31;
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t k = gid / L;
     const int sub = (int)(gid % L);
@@ -131,26 +136,18 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
     float pp = 0.f, qp = 0.f;
     long long nz = 0;
     int first_idx = -1, last_idx = -2;
-    int64_t ray = 0;
+    int ray = 0;
     if (active) {
-        int w = find_item(a.items, sd.w0, sd.w1, k);
-        const WorkItem it = a.items[w];
-        int64_t within = k - it.ray_off;
-        int wu = it.u1 - it.u0;
-        int ku = it.u0 + (int)(within % wu);
-        int kv = it.v0 + (int)(within / wu);
-        const DevView V = G.views[it.view];
-        const DevVT E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
-        float q[3], d[3];
-        ray_setup(G, V, E, ku, kv, q, d);
+        const RayRec rec = a.sb.table[(int64_t)slot * a.sb.table_stride + k];
+        ray = rec.ray;
         Box b = tile_box(t, DIM, 0, t.n[0], t.n[0] * t.n[1]);
         float tin, tout;
-        if (clip<DIM>(q, d, b, &tin, &tout)) {
+        if (clip<DIM>(rec.q, rec.inv, b, &tin, &tout)) {
             float dt = (tout - tin) * (1.0f / L);
             float t0 = sub == 0 ? tin : fmaf((float)sub, dt, tin);
             float t1 = sub == L - 1 ? tout : fmaf((float)(sub + 1), dt, tin);
             Kahan ax, ag;
-            nz = walk<DIM>(q, d, b, t0, t1, [&](int idx, float len) {
+            nz = walk<DIM>(rec.q, rec.inv, b, t0, t1, [&](int idx, float len) {
                 ax.add(len * __ldg(xj + idx));
                 ag.add(len * __ldg(gj + idx));
                 if (len > 0.f) {
@@ -161,7 +158,6 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
             pp = ax.s - ax.c;
             qp = ag.s - ag.c;
         }
-        ray = ray_index(G, it.view, ku, kv);
     }
     if (L > 1) {
         // a voxel cut by the split between two lanes was counted by both
@@ -176,28 +172,34 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
         a.sb.q[ray] = qv;
         qq = (double)qv * (double)qv;
     }
-    double bq = block_sum(qq, sh);
-    __syncthreads();
-    double bn = block_sum((double)nz, sh);
-    if (threadIdx.x == 0) {
-        a.sb.qq_part[(int64_t)slot * a.sb.max_fwd_blocks + blockIdx.x] = bq;
-        atomicAdd(a.sb.nnz, (unsigned long long)bn);
-        atomicAdd(a.sb.nnz_slot + slot, (unsigned long long)bn);
+    // per-warp partials, then the last warp of the slot finishes
+    const double wq = warp_sum(qq);
+    const long long wn = warp_sum_ll(nz);
+    const int nwarps_block = blockDim.x >> 5;
+    const int wglob = blockIdx.x * nwarps_block + (threadIdx.x >> 5);
+    const int total = gridDim.x * nwarps_block;
+    unsigned last = 0;
+    if (lane == 0) {
+        a.sb.qq_part[(int64_t)slot * a.sb.qq_stride + wglob] = wq;
+        if (wn) {
+            atomicAdd(a.sb.nnz, (unsigned long long)wn);
+            atomicAdd(a.sb.nnz_slot + slot, (unsigned long long)wn);
+        }
         __threadfence();
         unsigned prev = atomicAdd(a.sb.counters + slot, 1u);
-        last = prev == gridDim.x - 1;
+        last = prev == (unsigned)(total - 1);
     }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        // fixed-order sums: deterministic
-        double qs = 0.0;
-        for (int bb = 0; bb < (int)gridDim.x; ++bb)
-            qs += __ldcg(a.sb.qq_part + (int64_t)slot * a.sb.max_fwd_blocks + bb);
-        const int ngg = a.n_gg;
-        double gs = 0.0;
-        for (int bb = 0; bb < ngg; ++bb)
-            gs += __ldcg(a.sb.gg_part + (int64_t)slot * a.sb.gg_stride + bb);
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    // fixed-order sums (lane l takes partials l, l+32, ...; then a fixed butterfly)
+    double qs = 0.0;
+    for (int w = lane; w < total; w += 32) qs += __ldcg(a.sb.qq_part + (int64_t)slot * a.sb.qq_stride + w);
+    qs = warp_sum(qs);
+    double gs = 0.0;
+    for (int w = lane; w < a.n_gg; w += 32) gs += __ldcg(a.sb.gg_part + (int64_t)slot * a.sb.gg_stride + w);
+    gs = warp_sum(gs);
+    if (lane == 0) {
         double mu = qs > 0.0 ? sd.beta * gs / qs : 0.0;
         a.sb.mu[slot] = mu;
         unsigned long long nzs = atomicExch(a.sb.nnz_slot + slot, 0ull);
@@ -239,16 +241,18 @@ __device__ __forceinline__ void ray_table_body(const TableArgs& a, const WorkIte
     int kv = it.v0 + (int)(within / wu);
     const DevView V = G.views[it.view];
     const DevVT E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
-    float q[3], d[3];
+    float q[3], d[3], inv[3];
     ray_setup(G, V, E, ku, kv, q, d);
+    reciprocal(d, inv);
     RayRec rec;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         rec.q[c] = q[c];
-        rec.inv[c] = d[c] != 0.f ? 1.0f / d[c] : INFINITY;
+        rec.inv[c] = inv[c];
     }
-    rec.r = __ldg(a.r + ray_index(G, it.view, ku, kv));
-    rec.pad = 0.f;
+    const int64_t ray = ray_index(G, it.view, ku, kv);
+    rec.r = __ldg(a.r + ray);
+    rec.ray = (int32_t)ray;
     a.table[(int64_t)slot * a.slot_stride + k] = rec;
 }
 
@@ -318,7 +322,7 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
             const DevView V = G.views[it.view];
             const DevVT& E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
             float wu, wv;
-            detector_coord(G, V, P, &wu, &wv);
+            bin_coord_fast(G, V, P, &wu, &wv);
             const float hu = E.hw_u;
             int ku0 = max(it.u0, (int)ceilf(wu - 0.5f - hu));
             int ku1 = min(it.u1 - 1, (int)floorf(wu - 0.5f + hu));
@@ -329,6 +333,7 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
                 kv1 = min(it.v1 - 1, (int)floorf(wv - 0.5f + hv));
             }
             const int wdt = it.u1 - it.u0;
+            float view_sum = 0.f;  // 2-9 terms; compensated across views below
             for (int kv = kv0; kv <= kv1; ++kv) {
                 const int64_t rowoff = it.ray_off + (int64_t)(kv - it.v0) * wdt - it.u0;
                 for (int ku = ku0; ku <= ku1; ++ku) {
@@ -347,9 +352,10 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
                         }
                     }
                     float len = hit ? fmaxf(tout - tin, 0.f) : 0.f;
-                    acc.add(len * rec.r);
+                    view_sum = fmaf(len, rec.r, view_sum);
                 }
             }
+            acc.add(view_sum);
         }
     }
     part[threadIdx.x] = acc.s - acc.c;
@@ -681,7 +687,7 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     const int L = lanes_per_ray(b.max_rays * b.nslots, sm_count);
     int64_t nb = (b.max_rays * L + kFwdThreads - 1) / kFwdThreads;
     if (nb < 1) nb = 1;
-    if (nb > sb.max_fwd_blocks) return cudaErrorInvalidValue;
+    if (nb > sb.max_fwd_blocks || nb * (kFwdThreads / 32) > sb.qq_stride) return cudaErrorInvalidValue;
     dim3 grid((unsigned)nb, b.nslots);
     if (G.dim == 2) {
         if (L == 1) k_forward_dual<2, 1><<<grid, kFwdThreads, 0, s>>>(f);

@@ -65,7 +65,8 @@ struct SolverBuffers {
     int gg_stride;
     RayRec* table;   // [slot][table_stride]: ray table of the batch
     int64_t table_stride;
-    double* qq_part; // [slot][max_fwd_blocks]
+    double* qq_part; // [slot][qq_stride]: q^T q per forward warp
+    int qq_stride;
     unsigned int* counters;  // [slot]
     double* mu;      // [slot]
     double* hist;    // [step][kHistCols] = beta, gg, qq, mu, nnz
