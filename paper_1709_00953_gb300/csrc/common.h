@@ -49,7 +49,7 @@ struct DevTile {
     int64_t voff;   // start of the tile in tile-major volume storage
 };
 
-struct WorkItem {
+struct alignas(16) WorkItem {
     int32_t view;
     int32_t slot;          // step slot within a launch
     int32_t u0, u1, v0, v1;  // bins to process (inside the DevVT rectangle)
@@ -75,11 +75,9 @@ struct DevGeom {
 // Per-ray table of one launch (ray set-up done once, read by the
 // backprojection): tile-centred point q, reciprocal direction 1/d (infinite
 // where d = 0) and the residual r of the ray.
-struct RayRec {
-    float q[3];
-    float r;
-    float inv[3];
-    int32_t ray;  // index of the ray in the sinogram (below 2^31)
+struct alignas(16) RayRec {
+    float a[4];  // q[0], q[1], inv[0], inv[1]
+    float b[4];  // r, q[2], inv[2], index of the ray in the sinogram (int bits, < 2^31)
 };
 
 // One step of the solver as the kernels see it.

@@ -138,16 +138,20 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
     int first_idx = -1, last_idx = -2;
     int ray = 0;
     if (active) {
-        const RayRec rec = a.sb.table[(int64_t)slot * a.sb.table_stride + k];
-        ray = rec.ray;
+        const RayRec* rp = a.sb.table + (int64_t)slot * a.sb.table_stride + k;
+        const float4 ra = *reinterpret_cast<const float4*>(rp->a);
+        const float4 rb = *reinterpret_cast<const float4*>(rp->b);
+        ray = __float_as_int(rb.w);
+        const float q[3] = {ra.x, ra.y, rb.y};
+        const float inv[3] = {ra.z, ra.w, rb.z};
         Box b = tile_box(t, DIM, 0, t.n[0], t.n[0] * t.n[1]);
         float tin, tout;
-        if (clip<DIM>(rec.q, rec.inv, b, &tin, &tout)) {
+        if (clip<DIM>(q, inv, b, &tin, &tout)) {
             float dt = (tout - tin) * (1.0f / L);
             float t0 = sub == 0 ? tin : fmaf((float)sub, dt, tin);
             float t1 = sub == L - 1 ? tout : fmaf((float)(sub + 1), dt, tin);
             Kahan ax, ag;
-            nz = walk<DIM>(rec.q, rec.inv, b, t0, t1, [&](int idx, float len) {
+            nz = walk<DIM>(q, inv, b, t0, t1, [&](int idx, float len) {
                 ax.add(len * __ldg(xj + idx));
                 ag.add(len * __ldg(gj + idx));
                 if (len > 0.f) {
@@ -244,16 +248,11 @@ __device__ __forceinline__ void ray_table_body(const TableArgs& a, const WorkIte
     float q[3], d[3], inv[3];
     ray_setup(G, V, E, ku, kv, q, d);
     reciprocal(d, inv);
-    RayRec rec;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        rec.q[c] = q[c];
-        rec.inv[c] = inv[c];
-    }
     const int64_t ray = ray_index(G, it.view, ku, kv);
-    rec.r = __ldg(a.r + ray);
-    rec.ray = (int32_t)ray;
-    a.table[(int64_t)slot * a.slot_stride + k] = rec;
+    RayRec* dst = a.table + (int64_t)slot * a.slot_stride + k;
+    *reinterpret_cast<float4*>(dst->a) = make_float4(q[0], q[1], inv[0], inv[1]);
+    *reinterpret_cast<float4*>(dst->b) =
+        make_float4(__ldg(a.r + ray), q[2], inv[2], __int_as_float((int)ray));
 }
 
 template <int DIM>
@@ -290,11 +289,22 @@ struct BPArgs {
 // i.e. the very crossings the forward walk evaluates, so forward and adjoint use
 // the same lengths.  No atomics: the C CTAs of a cluster (one per view chunk)
 // add their partial sums through distributed shared memory in a fixed order.
+// Per-view data of a backprojection CTA, staged in shared memory.
+struct ViewCtx {
+    float S[3], dc[3], eu[3], ev[3];
+    float sdd;
+    float hw_u, hw_v;
+    int u0, u1, v0, v1;
+    int64_t ray_off;
+};
+constexpr int kViewBatch = 96;
+
 template <int DIM>
 __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem* items,
                                                  const StepDesc& sd, int slot) {
     __shared__ float part[kBPThreads];
     __shared__ double sh[kBPThreads / 32];
+    __shared__ ViewCtx vs[kViewBatch];
     cg::cluster_group cluster = cg::this_cluster();
     const DevGeom& G = a.G;
     const int C = (int)cluster.num_blocks();
@@ -315,44 +325,92 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
 #pragma unroll
     for (int c = 0; c < 3; ++c) P[c] = c < DIM ? t.T[c] + lo[c] + 0.5f : 0.f;
     const RayRec* __restrict__ tab = a.table + (int64_t)slot * a.table_stride;
+    // views of this chunk: items w0 + chunk, w0 + chunk + C, ...
+    const int n_mine = sd.w1 - sd.w0 > chunk ? (sd.w1 - sd.w0 - chunk + C - 1) / C : 0;
     Kahan acc;
-    if (valid) {
-        for (int w = sd.w0 + chunk; w < sd.w1; w += C) {
-            const WorkItem it = items[w];
-            const DevView V = G.views[it.view];
+    for (int base = 0; base < n_mine; base += kViewBatch) {
+        const int nb = min(kViewBatch, n_mine - base);
+        __syncthreads();
+        if ((int)threadIdx.x < nb) {
+            const WorkItem it = items[sd.w0 + chunk + (base + threadIdx.x) * C];
+            const DevView& V = G.views[it.view];
             const DevVT& E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
+            ViewCtx& c = vs[threadIdx.x];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                c.S[k] = V.S[k];
+                c.dc[k] = V.dc[k];
+                c.eu[k] = V.eu[k];
+                c.ev[k] = V.ev[k];
+            }
+            c.sdd = V.sdd;
+            c.hw_u = E.hw_u;
+            c.hw_v = E.hw_v;
+            c.u0 = it.u0;
+            c.u1 = it.u1;
+            c.v0 = it.v0;
+            c.v1 = it.v1;
+            c.ray_off = it.ray_off;
+        }
+        __syncthreads();
+        if (!valid) continue;
+        for (int i = 0; i < nb; ++i) {
+            const ViewCtx& c = vs[i];
+            DevView V;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                V.S[k] = c.S[k];
+                V.dc[k] = c.dc[k];
+                V.eu[k] = c.eu[k];
+                V.ev[k] = c.ev[k];
+            }
+            V.sdd = c.sdd;
             float wu, wv;
             bin_coord_fast(G, V, P, &wu, &wv);
-            const float hu = E.hw_u;
-            int ku0 = max(it.u0, (int)ceilf(wu - 0.5f - hu));
-            int ku1 = min(it.u1 - 1, (int)floorf(wu - 0.5f + hu));
-            int kv0 = it.v0, kv1 = it.v1 - 1;
+            int ku0 = max(c.u0, (int)ceilf(wu - 0.5f - c.hw_u));
+            int ku1 = min(c.u1 - 1, (int)floorf(wu - 0.5f + c.hw_u));
+            int kv0 = c.v0, kv1 = c.v1 - 1;
             if (DIM == 3) {
-                const float hv = E.hw_v;
-                kv0 = max(it.v0, (int)ceilf(wv - 0.5f - hv));
-                kv1 = min(it.v1 - 1, (int)floorf(wv - 0.5f + hv));
+                kv0 = max(c.v0, (int)ceilf(wv - 0.5f - c.hw_v));
+                kv1 = min(c.v1 - 1, (int)floorf(wv - 0.5f + c.hw_v));
             }
-            const int wdt = it.u1 - it.u0;
-            float view_sum = 0.f;  // 2-9 terms; compensated across views below
+            const int wdt = c.u1 - c.u0;
+            float view_sum = 0.f;  // a few terms; compensated across views below
             for (int kv = kv0; kv <= kv1; ++kv) {
-                const int64_t rowoff = it.ray_off + (int64_t)(kv - it.v0) * wdt - it.u0;
+                const int64_t rowoff = c.ray_off + (int64_t)(kv - c.v0) * wdt - c.u0;
                 for (int ku = ku0; ku <= ku1; ++ku) {
-                    const RayRec rec = tab[rowoff + ku];
+                    const RayRec* rp = tab + rowoff + ku;
+                    const float4 ra = *reinterpret_cast<const float4*>(rp->a);
+                    float q[3], inv[3], r;
+                    q[0] = ra.x;
+                    q[1] = ra.y;
+                    inv[0] = ra.z;
+                    inv[1] = ra.w;
+                    if (DIM == 3) {
+                        const float4 rb = *reinterpret_cast<const float4*>(rp->b);
+                        r = rb.x;
+                        q[2] = rb.y;
+                        inv[2] = rb.z;
+                    } else {
+                        r = rp->b[0];
+                        q[2] = 0.f;
+                        inv[2] = INFINITY;
+                    }
                     float tin = -INFINITY, tout = INFINITY;
                     bool hit = true;
 #pragma unroll
-                    for (int c = 0; c < DIM; ++c) {
-                        if (isfinite(rec.inv[c])) {
-                            float ta = (lo[c] - rec.q[c]) * rec.inv[c];
-                            float tb = (lo[c] + 1.0f - rec.q[c]) * rec.inv[c];
+                    for (int k = 0; k < DIM; ++k) {
+                        if (isfinite(inv[k])) {
+                            float ta = (lo[k] - q[k]) * inv[k];
+                            float tb = (lo[k] + 1.0f - q[k]) * inv[k];
                             tin = fmaxf(tin, fminf(ta, tb));
                             tout = fminf(tout, fmaxf(ta, tb));
                         } else {
-                            hit = hit && rec.q[c] >= lo[c] && rec.q[c] < lo[c] + 1.0f;
+                            hit = hit && q[k] >= lo[k] && q[k] < lo[k] + 1.0f;
                         }
                     }
                     float len = hit ? fmaxf(tout - tin, 0.f) : 0.f;
-                    view_sum = fmaf(len, rec.r, view_sum);
+                    view_sum = fmaf(len, r, view_sum);
                 }
             }
             acc.add(view_sum);
