@@ -224,15 +224,23 @@ __device__ __forceinline__ int traverse(const float q[3], const float inv[3], co
     return walk<DIM>(q, inv, b, tin, tout, f);
 }
 
-// Fast bin coordinates of a point, for choosing candidate bins only (points
-// whose rays reach the detector): correctly rounded reciprocal instead of a
-// division and, when the curved detector spans |gamma| < 0.46 rad, atan by its
-// Taylor series to x^11 (error below |x|^13 / 13 < 1.5e-5 rad on |x| <= 0.5).
-__device__ __forceinline__ void bin_coord_fast(const DevGeom& G, const DevView& V, const float P[3],
-                                               float* wu, float* wv) {
+// Bin coordinates (wu, wv) of a voxel centre P and the half-widths (hu, hv) of
+// the voxel's shadow, for choosing the candidate bins of a voxel: the shadow of
+// the unit voxel is [w - h1, w + h1] to first order, h1 = 0.5 sum_k |dw/dP_k|;
+// the second derivative of a perspective or angular map is at most ~2 |grad w|
+// / depth, so over half a voxel diagonal (|delta|^2 <= 3/4) the second-order
+// term is below 0.75 |grad w| / depth <= 1.5 h1 / depth: h = h1 (1 + 1.5 /
+// depth).  Callers add a small margin for rounding.  Uses a correctly
+// rounded reciprocal instead of divisions and, when the curved detector spans
+// |gamma| < 0.46 rad, atan by its Taylor series to x^11 (error below
+// |x|^13 / 13 < 1e-5 rad on |x| <= 0.5).
+__device__ __forceinline__ void voxel_shadow(const DevGeom& G, const DevView& V, const float P[3],
+                                             float* wu, float* wv, float* hu, float* hv) {
     if (G.kind == PARALLEL_2D) {
         *wu = fmaf(P[0] * V.eu[0] + P[1] * V.eu[1], G.inv_pu, 0.5f * G.nu);
+        *hu = 0.5f * (fabsf(V.eu[0]) + fabsf(V.eu[1])) * G.inv_pu;
         *wv = 0.5f;
+        *hv = 0.f;
         return;
     }
     float r0 = P[0] - V.S[0], r1 = P[1] - V.S[1], r2 = P[2] - V.S[2];
@@ -240,30 +248,45 @@ __device__ __forceinline__ void bin_coord_fast(const DevGeom& G, const DevView& 
     float lu = r0 * V.eu[0] + r1 * V.eu[1] + r2 * V.eu[2];
     float rd = __frcp_rn(depth);
     if (G.kind == FAN_2D_CURVED) {
-        if (!G.fast_arc) {
-            *wu = fmaf(atan2f(lu, depth), G.inv_pu, 0.5f * G.nu);
-            *wv = 0.5f;
-            return;
+        float x = lu * rd;  // tan(gamma)
+        float gam;
+        if (G.fast_arc) {
+            float x2 = x * x;
+            float p = fmaf(x2, -1.0f / 11.0f, 1.0f / 9.0f);
+            p = fmaf(x2, p, -1.0f / 7.0f);
+            p = fmaf(x2, p, 1.0f / 5.0f);
+            p = fmaf(x2, p, -1.0f / 3.0f);
+            p = fmaf(x2, p, 1.0f);
+            gam = x * p;
+        } else {
+            gam = atan2f(lu, depth);
         }
-        float x = lu * rd;  // tan(gamma); |gamma| < 0.46 on the detector
-        float x2 = x * x;
-        float p = fmaf(x2, -1.0f / 11.0f, 1.0f / 9.0f);
-        p = fmaf(x2, p, -1.0f / 7.0f);
-        p = fmaf(x2, p, 1.0f / 5.0f);
-        p = fmaf(x2, p, -1.0f / 3.0f);
-        p = fmaf(x2, p, 1.0f);
-        *wu = fmaf(x * p, G.inv_pu, 0.5f * G.nu);
+        *wu = fmaf(gam, G.inv_pu, 0.5f * G.nu);
+        // d gamma / dP = (depth e_u - lu d_c) / (depth^2 + lu^2)
+        float sc = 0.5f * G.inv_pu * __frcp_rn(fmaf(depth, depth, lu * lu));
+        *hu = sc * (fabsf(depth * V.eu[0] - lu * V.dc[0]) + fabsf(depth * V.eu[1] - lu * V.dc[1])) *
+              fmaf(1.5f, rd, 1.0f);
         *wv = 0.5f;
+        *hv = 0.f;
         return;
     }
+    // flat detector: w = sdd * l / depth / pitch, dw/dP = sdd (depth e - l d_c) / depth^2 / pitch
     float lam = V.sdd * rd;
     *wu = fmaf(lam * lu, G.inv_pu, 0.5f * G.nu);
+    float sc = 0.5f * lam * rd * fmaf(1.5f, rd, 1.0f);
+    float hu_ = fabsf(depth * V.eu[0] - lu * V.dc[0]) + fabsf(depth * V.eu[1] - lu * V.dc[1]);
     if (G.dim == 3) {
         float lv = r0 * V.ev[0] + r1 * V.ev[1] + r2 * V.ev[2];
         *wv = fmaf(lam * lv, G.inv_pv, 0.5f * G.nv);
+        hu_ += fabsf(depth * V.eu[2] - lu * V.dc[2]);
+        float hv_ = fabsf(depth * V.ev[0] - lv * V.dc[0]) + fabsf(depth * V.ev[1] - lv * V.dc[1]) +
+                    fabsf(depth * V.ev[2] - lv * V.dc[2]);
+        *hv = sc * hv_ * G.inv_pv;
     } else {
         *wv = 0.5f;
+        *hv = 0.f;
     }
+    *hu = sc * hu_ * G.inv_pu;
 }
 
 // Compensated (Kahan) accumulator for the FP32 ray sums.

@@ -298,6 +298,9 @@ struct ViewCtx {
     int64_t ray_off;
 };
 constexpr int kViewBatch = 96;
+// bins added on each side of a voxel's shadow window: covers the series atan
+// (below 0.011 bin at the finest pitch used) and FP32 rounding
+constexpr float kShadowMargin = 0.02f;
 
 template <int DIM>
 __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem* items,
@@ -365,14 +368,16 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
                 V.ev[k] = c.ev[k];
             }
             V.sdd = c.sdd;
-            float wu, wv;
-            bin_coord_fast(G, V, P, &wu, &wv);
-            int ku0 = max(c.u0, (int)ceilf(wu - 0.5f - c.hw_u));
-            int ku1 = min(c.u1 - 1, (int)floorf(wu - 0.5f + c.hw_u));
+            float wu, wv, hu, hv;
+            voxel_shadow(G, V, P, &wu, &wv, &hu, &hv);
+            hu += kShadowMargin;
+            int ku0 = max(c.u0, (int)ceilf(wu - 0.5f - hu));
+            int ku1 = min(c.u1 - 1, (int)floorf(wu - 0.5f + hu));
             int kv0 = c.v0, kv1 = c.v1 - 1;
             if (DIM == 3) {
-                kv0 = max(c.v0, (int)ceilf(wv - 0.5f - c.hw_v));
-                kv1 = min(c.v1 - 1, (int)floorf(wv - 0.5f + c.hw_v));
+                hv += kShadowMargin;
+                kv0 = max(c.v0, (int)ceilf(wv - 0.5f - hv));
+                kv1 = min(c.v1 - 1, (int)floorf(wv - 0.5f + hv));
             }
             const int wdt = c.u1 - c.u0;
             float view_sum = 0.f;  // a few terms; compensated across views below
