@@ -40,6 +40,24 @@ from synth import data as D  # noqa: E402
 ALG_FLOP = {"backproject": 6.0, "forward_dual": 8.0}
 FP32_LANES_PER_SM = 128
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of
+# the fan2d_512 workload (profiles/fan2d_512_kernels_ncu.md), valid only for the
+# kernel sources they were taken from (hash of ops.cu, device.cuh, common.h).
+NCU_TRAFFIC = {
+    ("fan2d_512_720x768_8x16_importance", "96171a63424e9d9d"): {
+        "backproject": 2078976 + 512, "forward_dual": 2330880},
+}
+KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/csrc/device.cuh",
+                  "paper_1709_00953_gb300/csrc/common.h")
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -305,8 +323,9 @@ def run_gpu(args, cfg, world, rank, local):
     peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
     flop = ALG_FLOP[dom] * nnz_per_solve * args.steps
     achieved = flop / (kern[dom]["ms"] / 1e3) / 1e12
+    traffic = NCU_TRAFFIC.get((cfg["name"], kernel_hash()), {}).get(dom)
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops,
-            "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
             "peak_basis": "FP32 FMA: %d SMs x %d lanes x 2 x %.0f MHz (median SM clock of this run)"
                           % (sm_count, FP32_LANES_PER_SM, mhz),
             "flop_per_nnz": ALG_FLOP[dom]}
