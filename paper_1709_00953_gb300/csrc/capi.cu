@@ -440,6 +440,13 @@ int execute_plan(csgd_solver* S, Plan& pl, cudaStream_t s) {
         b.nslots = op.n;
         b.j = op.j;
         b.max_rays = op.max_rays;
+        b.w_begin = pl.steps[op.first].w0;
+        b.n_items = pl.steps[op.first + op.n - 1].w1 - b.w_begin;
+        b.max_item_rays = 0;
+        for (int w = b.w_begin; w < b.w_begin + b.n_items; ++w)
+            b.max_item_rays = std::max<int64_t>(
+                b.max_item_rays,
+                (int64_t)(pl.items[w].u1 - pl.items[w].u0) * (pl.items[w].v1 - pl.items[w].v0));
         b.sync_epoch = S->prm.sync == CSGD_SYNC_EPOCH;
         cudaEvent_t evs[4];
         int e0 = 0;
@@ -759,7 +766,7 @@ static int64_t footprint(const csgd_partition* P, const csgd_solver_params* prm,
     b += 4 * (4 * ny);                           // y, r, p, q
     if (prm->sync == CSGD_SYNC_EPOCH) b += 4 * ny;  // pending residual change
     b += 4 * std::max<int64_t>(1, p.z_floats);   // z store
-    b += 4 * (int64_t)(*max_slots) * p.max_tile_voxels;  // g per slot
+    b += 8 * (int64_t)(*max_slots) * p.max_tile_voxels;  // (x, g) pairs per slot
     b += (int64_t)sizeof(RayRec) * (*max_slots) * (*max_rays);  // ray tables
     b += 8 * (int64_t)(*max_slots) * (*n_gg + 8 * *fwd_blocks + 1) + 4 * (*max_slots);
     return b;
@@ -823,7 +830,7 @@ int32_t csgd_solver_create(const csgd_partition* Pc, const csgd_solver_params* p
     if (params->sync == CSGD_SYNC_EPOCH) ALLOC(b.d, sizeof(float) * S->n_rays, "cudaMalloc(d)");
     ALLOC(b.p, sizeof(float) * S->n_rays, "cudaMalloc(p)");
     ALLOC(b.q, sizeof(float) * S->n_rays, "cudaMalloc(q)");
-    ALLOC(b.g, sizeof(float) * b.max_slots * b.g_stride, "cudaMalloc(g)");
+    ALLOC(b.g, 2 * sizeof(float) * b.max_slots * b.g_stride, "cudaMalloc(x, g pairs)");
     ALLOC(b.gg_part, sizeof(double) * b.max_slots * ng, "cudaMalloc(gg partials)");
     ALLOC(b.table, sizeof(RayRec) * b.max_slots * b.table_stride, "cudaMalloc(ray tables)");
     b.qq_stride = b.max_fwd_blocks * 8;

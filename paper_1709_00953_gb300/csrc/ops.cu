@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
     const int slot = blockIdx.y;
     const StepDesc sd = a.steps[a.first + slot];
     const DevTile t = G.tiles[sd.j];
-    const float* __restrict__ xj = a.sb.x + t.voff;
-    const float* __restrict__ gj = a.sb.g + (int64_t)slot * a.sb.g_stride;
+    // (x_J, g_J) interleaved per voxel by the backprojection: one 8-byte gather per voxel
+    const float2* __restrict__ xg = reinterpret_cast<const float2*>(a.sb.g) + (int64_t)slot * a.sb.g_stride;
     const int lane = threadIdx.x & 31;
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t k = gid / L;
@@ -152,8 +152,9 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
             float t1 = sub == L - 1 ? tout : fmaf((float)(sub + 1), dt, tin);
             Kahan ax, ag;
             nz = walk<DIM>(q, inv, b, t0, t1, [&](int idx, float len) {
-                ax.add(len * __ldg(xj + idx));
-                ag.add(len * __ldg(gj + idx));
+                const float2 e = __ldg(xg + idx);
+                ax.add(len * e.x);
+                ag.add(len * e.y);
                 if (len > 0.f) {
                     if (first_idx < 0) first_idx = idx;
                     last_idx = idx;
@@ -222,51 +223,49 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
 // ---------------------------------------------------------------------------
 // backprojection
 // ---------------------------------------------------------------------------
-// Ray table of a launch: every ray of every slot, set up once.
+// Ray table of a launch: every ray of every slot, set up once.  One CTA row per
+// work item (view), so a thread knows its ray without searching.
 struct TableArgs {
     DevGeom G;
-    int first;
+    int j;               // tile of the launch
+    int w_begin;         // first work item of the launch
     const float* r;
     RayRec* table;       // [slot][ray slot]
     int64_t slot_stride;
 };
 
 template <int DIM>
-__device__ __forceinline__ void ray_table_body(const TableArgs& a, const WorkItem* items,
-                                               const StepDesc& sd, int slot) {
+__device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkItem& it) {
     const DevGeom& G = a.G;
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= sd.n_rays) return;
-    int w = find_item(items, sd.w0, sd.w1, k);
-    const WorkItem it = items[w];
-    int64_t within = k - it.ray_off;
-    int wu = it.u1 - it.u0;
-    int ku = it.u0 + (int)(within % wu);
-    int kv = it.v0 + (int)(within / wu);
     const DevView V = G.views[it.view];
-    const DevVT E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
-    float q[3], d[3], inv[3];
-    ray_setup(G, V, E, ku, kv, q, d);
-    reciprocal(d, inv);
-    const int64_t ray = ray_index(G, it.view, ku, kv);
-    RayRec* dst = a.table + (int64_t)slot * a.slot_stride + k;
-    *reinterpret_cast<float4*>(dst->a) = make_float4(q[0], q[1], inv[0], inv[1]);
-    *reinterpret_cast<float4*>(dst->b) =
-        make_float4(__ldg(a.r + ray), q[2], inv[2], __int_as_float((int)ray));
+    const DevVT E = G.vt[(int64_t)it.view * G.n_tiles + a.j];
+    const int wu = it.u1 - it.u0;
+    const int nr = wu * (it.v1 - it.v0);
+    RayRec* dst = a.table + (int64_t)it.slot * a.slot_stride + it.ray_off;
+    for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < nr; k += gridDim.y * blockDim.x) {
+        const int ku = it.u0 + k % wu;
+        const int kv = it.v0 + k / wu;
+        float q[3], d[3], inv[3];
+        ray_setup(G, V, E, ku, kv, q, d);
+        reciprocal(d, inv);
+        const int64_t ray = ray_index(G, it.view, ku, kv);
+        *reinterpret_cast<float4*>(dst[k].a) = make_float4(q[0], q[1], inv[0], inv[1]);
+        *reinterpret_cast<float4*>(dst[k].b) =
+            make_float4(__ldg(a.r + ray), q[2], inv[2], __int_as_float((int)ray));
+    }
 }
 
 template <int DIM>
 __global__ void __launch_bounds__(256) k_ray_table_inline(const TableArgs a,
                                                           const __grid_constant__ InlineItems it) {
-    ray_table_body<DIM>(a, it.items, it.step, 0);
+    ray_table_item<DIM>(a, it.items[blockIdx.x]);
 }
 
 template <int DIM>
 __global__ void __launch_bounds__(256) k_ray_table_solver(const TableArgs a,
-                                                          const WorkItem* __restrict__ items,
-                                                          const StepDesc* __restrict__ steps) {
-    const StepDesc sd = steps[a.first + blockIdx.y];
-    ray_table_body<DIM>(a, items, sd, blockIdx.y);
+                                                          const WorkItem* __restrict__ items) {
+    const WorkItem it = items[a.w_begin + blockIdx.x];
+    ray_table_item<DIM>(a, it);
 }
 
 struct BPArgs {
@@ -274,7 +273,9 @@ struct BPArgs {
     int first;
     const RayRec* table;   // [slot][ray slot]
     int64_t table_stride;
-    float* gout;           // tile-local scratch (mode 0) or row-major volume (mode 1)
+    const float* xt;       // mode 0: tile-major x, copied next to g
+    float* gout;           // mode 0: (x_J, g_J) pairs per slot, tile-local; mode 1:
+                           // row-major volume
     int mode;
     int accumulate;
     int64_t slot_stride;
@@ -430,7 +431,8 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
         s *= G.h;
         if (valid) {
             if (a.mode == 0) {
-                a.gout[(int64_t)slot * a.slot_stride + v] = s;
+                reinterpret_cast<float2*>(a.gout)[(int64_t)slot * a.slot_stride + v] =
+                    make_float2(a.xt[t.voff + v], s);
             } else {
                 int64_t gi = ((int64_t)(t.lo[2] + x2) * G.ny + (t.lo[1] + x1)) * G.nx + t.lo[0] + x0;
                 a.gout[gi] = a.accumulate ? a.gout[gi] + s : s;
@@ -468,27 +470,29 @@ struct EpiArgs {
     int first;
     int nslots;
     int j;
+    int w_begin;     // first work item of the batch
+    int n_items;     // work items of the batch (CTA rows 0 .. n_items-1)
     int sync_epoch;
     SolverBuffers sb;
 };
 
+// CTAs 0 .. n_items-1 (x) update z and r on one work item's rays each; the
+// remaining CTAs add the batch's candidates into x^ of the tile.
 __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
     const DevGeom& G = a.G;
-    if ((int)blockIdx.y < a.nslots) {
-        const int slot = blockIdx.y;
-        const StepDesc sd = a.steps[a.first + slot];
-        const float mu = (float)a.sb.mu[slot];
-        for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < sd.n_rays;
-             k += (int64_t)gridDim.x * blockDim.x) {
-            int w = find_item(a.items, sd.w0, sd.w1, k);
-            const WorkItem it = a.items[w];
-            int64_t within = k - it.ray_off;
-            int wu = it.u1 - it.u0;
-            int ku = it.u0 + (int)(within % wu);
-            int kv = it.v0 + (int)(within / wu);
-            const DevVT& E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
-            int64_t zi = E.zoff + (int64_t)(kv - E.v0) * (E.u1 - E.u0) + (ku - E.u0);
-            int64_t ray = ray_index(G, it.view, ku, kv);
+    if ((int)blockIdx.x < a.n_items) {
+        const WorkItem it = a.items[a.w_begin + blockIdx.x];
+        const float mu = (float)a.sb.mu[it.slot];
+        const DevVT& E = G.vt[(int64_t)it.view * G.n_tiles + a.j];
+        const int ew = E.u1 - E.u0;
+        const int64_t zbase = E.zoff - (int64_t)E.v0 * ew - E.u0;
+        const int wu = it.u1 - it.u0;
+        const int nr = wu * (it.v1 - it.v0);
+        for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < nr; k += gridDim.y * blockDim.x) {
+            const int ku = it.u0 + k % wu;
+            const int kv = it.v0 + k / wu;
+            const int64_t zi = zbase + (int64_t)kv * ew + ku;
+            const int64_t ray = ray_index(G, it.view, ku, kv);
             float zn = fmaf(mu, a.sb.q[ray], a.sb.p[ray]);
             float zo = a.sb.z[zi];
             a.sb.z[zi] = zn;
@@ -500,15 +504,18 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
         const int64_t nv = (int64_t)t.n[0] * t.n[1] * t.n[2];
         float* xh = a.sb.xh + t.voff;
         const float* x = a.sb.x + t.voff;
-        for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv;
-             v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t nthreads = (int64_t)(gridDim.x - a.n_items) * gridDim.y * blockDim.x;
+        int64_t v0 = ((int64_t)(blockIdx.x - a.n_items) * gridDim.y + blockIdx.y) * blockDim.x +
+                     threadIdx.x;
+        for (int64_t v = v0; v < nv; v += nthreads) {
             float xv = x[v];
             float s = xh[v];
             for (int sl = 0; sl < a.nslots; ++sl)
-                s += fmaf((float)a.sb.mu[sl], a.sb.g[(int64_t)sl * a.sb.g_stride + v], xv);
+                s += fmaf((float)a.sb.mu[sl], a.sb.g[2 * ((int64_t)sl * a.sb.g_stride + v) + 1], xv);
             xh[v] = s;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.sb.cnt[a.j] += a.nslots;
+        if (blockIdx.x == a.n_items && blockIdx.y == 0 && threadIdx.x == 0)
+            a.sb.cnt[a.j] += a.nslots;
     }
 }
 
@@ -605,17 +612,24 @@ static cudaError_t launch_bp_common(const DevGeom& G, const BPPlan& plan, int ns
     return cudaLaunchKernelEx(&cfg, k_backproject_solver<3>, a, items, steps);
 }
 
-static cudaError_t launch_table(const DevGeom& G, int nslots, int64_t max_rays, cudaStream_t s,
-                                const TableArgs& t, const InlineItems* inl, const WorkItem* items,
-                                const StepDesc* steps) {
-    if (max_rays <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((max_rays + 255) / 256), nslots);
+// Rows of a per-item grid: enough CTAs per item to cover its rays with ~4
+// passes, at most 16.
+static int item_rows(int64_t max_item_rays) {
+    int64_t rows = (max_item_rays + 4 * 256 - 1) / (4 * 256);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(rows, 16));
+}
+
+static cudaError_t launch_table(const DevGeom& G, int n_items, int64_t max_item_rays,
+                                cudaStream_t s, const TableArgs& t, const InlineItems* inl,
+                                const WorkItem* items) {
+    if (n_items <= 0) return cudaSuccess;
+    dim3 grid((unsigned)n_items, (unsigned)item_rows(max_item_rays));
     if (inl) {
         if (G.dim == 2) k_ray_table_inline<2><<<grid, 256, 0, s>>>(t, *inl);
         else k_ray_table_inline<3><<<grid, 256, 0, s>>>(t, *inl);
     } else {
-        if (G.dim == 2) k_ray_table_solver<2><<<grid, 256, 0, s>>>(t, items, steps);
-        else k_ray_table_solver<3><<<grid, 256, 0, s>>>(t, items, steps);
+        if (G.dim == 2) k_ray_table_solver<2><<<grid, 256, 0, s>>>(t, items);
+        else k_ray_table_solver<3><<<grid, 256, 0, s>>>(t, items);
     }
     return cudaGetLastError();
 }
@@ -652,11 +666,16 @@ cudaError_t launch_backproject_inline(const DevGeom& G, const DevTile& tile,
                                       cudaStream_t s) {
     TableArgs ta;
     ta.G = G;
-    ta.first = 0;
+    ta.j = it.step.j;
+    ta.w_begin = 0;
     ta.r = r;
     ta.table = table;
     ta.slot_stride = 0;
-    cudaError_t e = launch_table(G, 1, it.step.n_rays, s, ta, &it, nullptr, nullptr);
+    int64_t max_item = 0;
+    for (int k = 0; k < it.n; ++k)
+        max_item = std::max<int64_t>(max_item, (int64_t)(it.items[k].u1 - it.items[k].u0) *
+                                                   (it.items[k].v1 - it.items[k].v0));
+    cudaError_t e = launch_table(G, it.n, max_item, s, ta, &it, nullptr);
     if (e != cudaSuccess) return e;
     BPPlan plan = plan_backprojection(G, tile, 1, sm_count);
     BPArgs a;
@@ -664,6 +683,7 @@ cudaError_t launch_backproject_inline(const DevGeom& G, const DevTile& tile,
     a.first = 0;
     a.table = table;
     a.table_stride = 0;
+    a.xt = nullptr;
     a.gout = g;
     a.mode = 1;
     a.accumulate = accumulate;
@@ -717,11 +737,12 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     // 1. g_J = (A_I^J)^T r_I per slot: ray table, then voxel-driven sums
     TableArgs ta;
     ta.G = G;
-    ta.first = b.first;
+    ta.j = b.j;
+    ta.w_begin = b.w_begin;
     ta.r = sb.r;
     ta.table = sb.table;
     ta.slot_stride = sb.table_stride;
-    cudaError_t e = launch_table(G, b.nslots, b.max_rays, s, ta, nullptr, items, steps);
+    cudaError_t e = launch_table(G, b.n_items, b.max_item_rays, s, ta, nullptr, items);
     if (e != cudaSuccess) return e;
     if (plan.blocks > sb.gg_stride) return cudaErrorInvalidValue;
     BPArgs a;
@@ -729,6 +750,7 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     a.first = b.first;
     a.table = sb.table;
     a.table_stride = sb.table_stride;
+    a.xt = sb.x;
     a.gout = sb.g;
     a.mode = 0;
     a.accumulate = 0;
@@ -772,11 +794,15 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     ea.first = b.first;
     ea.nslots = b.nslots;
     ea.j = b.j;
+    ea.w_begin = b.w_begin;
+    ea.n_items = b.n_items;
     ea.sync_epoch = b.sync_epoch;
     ea.sb = sb;
-    int64_t eb = (b.max_rays + kEpiThreads - 1) / kEpiThreads;
-    eb = std::max<int64_t>(1, std::min<int64_t>(eb, 4 * sm_count));
-    k_epilogue<<<dim3((unsigned)eb, b.nslots + 1), kEpiThreads, 0, s>>>(ea);
+    const int rows = item_rows(b.max_item_rays);
+    const int64_t tv = (int64_t)tile.n[0] * tile.n[1] * tile.n[2];
+    const int64_t vox_blocks = std::max<int64_t>(1, (tv + (int64_t)kEpiThreads * rows - 1) /
+                                                       ((int64_t)kEpiThreads * rows));
+    k_epilogue<<<dim3((unsigned)(b.n_items + vox_blocks), rows), kEpiThreads, 0, s>>>(ea);
     e = cudaGetLastError();
     if (ev) cudaEventRecord(ev[3], s);
     return e;

@@ -60,7 +60,7 @@ struct SolverBuffers {
     // scratch
     float* p;        // A x_J per ray
     float* q;        // A g_J per ray
-    float* g;        // g_J per slot, tile-local [slot][max_tile_voxels]
+    float* g;        // (x_J, g_J) pairs per slot, tile-local [slot][g_stride][2]
     double* gg_part; // [slot][gg_stride]: g^T g per backprojection CTA
     int gg_stride;
     RayRec* table;   // [slot][table_stride]: ray table of the batch
@@ -82,7 +82,9 @@ struct BatchLaunch {
     int first;       // first step descriptor of the batch
     int nslots;      // steps in the batch (all on tile j)
     int j;
-    int64_t max_rays;
+    int64_t max_rays;        // rays of the largest step
+    int w_begin, n_items;    // work items of the batch (contiguous)
+    int64_t max_item_rays;   // rays of the largest work item
     int sync_epoch;
 };
 
