@@ -271,6 +271,30 @@ int32_t csgd_solve(csgd_solver* solver, int64_t n_steps, float* x_out, int32_t x
 int32_t csgd_solver_history(csgd_solver* solver, csgd_step_info* out, int64_t capacity,
                             int64_t* count);
 
+/* ---------------------------------------------------------------------------
+ * Solves as CUDA graphs, and many solves in one launch
+ * (the paper has no counterpart: these serve batched and repeated solves)
+ * ------------------------------------------------------------------------- */
+typedef struct csgd_graph csgd_graph;
+
+/* Captures a whole solve of this solver into a CUDA graph: reset to x = 0,
+ * z = 0, r = y (the solver's current y), then n_steps steps of the schedule
+ * from the seed, closing the epoch at the end, then x to x_out (device, or
+ * pinned host memory if x_on_host; may be NULL).  The schedule is planned and
+ * uploaded once, here; every launch repeats the same solve.  Launching the
+ * graph leaves the solver's host-side counters (epochs, steps) untouched, so
+ * mixing graph launches with csgd_solve needs a csgd_solver_reset in between.
+ * A solver's graph must not run concurrently with other work on that solver. */
+int32_t csgd_solver_graph_create(csgd_solver* solver, int64_t n_steps, float* x_out,
+                                 int32_t x_on_host, csgd_graph** out);
+/* One graph that runs the given solve graphs concurrently (child graphs without
+ * dependencies): all block steps of all problems in one launch.  The parts must
+ * belong to different solvers and must outlive nothing: the batch copies them. */
+int32_t csgd_graph_batch_create(csgd_graph* const* parts, int32_t n, csgd_graph** out);
+/* Enqueues the graph on the stream (asynchronous). */
+int32_t csgd_graph_launch(csgd_graph* graph, csgd_stream stream);
+int32_t csgd_graph_destroy(csgd_graph* graph);
+
 /* Per-kernel timing (the paper has no counterpart; it supports the roofline
  * measurements).  While enabled, every kernel launch of csgd_solve /
  * csgd_solve_step is bracketed by CUDA events on the caller's stream.

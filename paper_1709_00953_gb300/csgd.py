@@ -107,6 +107,10 @@ SIGNATURES = {
     "csgd_solve_step": ([_vp, ctypes.POINTER(BlockChoice), ctypes.POINTER(StepInfo), _vp], _i32),
     "csgd_solve": ([_vp, _i64, _vp, _i32, ctypes.POINTER(Report), _i32, _vp], _i32),
     "csgd_solver_history": ([_vp, ctypes.POINTER(StepInfo), _i64, ctypes.POINTER(_i64)], _i32),
+    "csgd_solver_graph_create": ([_vp, _i64, _vp, _i32, ctypes.POINTER(_vp)], _i32),
+    "csgd_graph_batch_create": ([ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp)], _i32),
+    "csgd_graph_launch": ([_vp, _vp], _i32),
+    "csgd_graph_destroy": ([_vp], _i32),
     "csgd_solver_profile": ([_vp, _i32], _i32),
     "csgd_solver_profile_read": ([_vp, ctypes.POINTER(KernelTimes), _i32], _i32),
     "csgd_last_error": ([], ctypes.c_char_p),
@@ -397,6 +401,18 @@ class Solver:
         return [dict(step=buf[k].step, beta=buf[k].beta, gg=buf[k].gg, qq=buf[k].qq, mu=buf[k].mu,
                      nnz=buf[k].nnz) for k in range(cnt.value)]
 
+    def graph(self, n_steps: int, x_out=None) -> "Graph":
+        """A CUDA graph of a whole solve (reset, n_steps steps, x to x_out)."""
+        if x_out is None:
+            ptr, host = None, 0
+        elif x_out.is_cuda:
+            ptr, host = _dev_ptr(x_out, "x_out", self.part.n_voxels), 0
+        else:
+            ptr, host = _host_ptr(x_out, "x_out", self.part.n_voxels), 1
+        h = ctypes.c_void_p()
+        _check(load().csgd_solver_graph_create(self.handle, int(n_steps), ptr, host, ctypes.byref(h)))
+        return Graph(h, [self, x_out])
+
     def profile(self, enable: bool = True):
         _check(load().csgd_solver_profile(self.handle, int(bool(enable))))
 
@@ -409,6 +425,30 @@ class Solver:
         if getattr(self, "handle", None) and _lib is not None:
             _lib.csgd_solver_destroy(self.handle)
             self.handle = None
+
+
+class Graph:
+    """A captured solve (or a batch of them); keeps its solvers and outputs alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        _check(load().csgd_graph_launch(self.handle, _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.csgd_graph_destroy(self.handle)
+            self.handle = None
+
+
+def graph_batch(graphs) -> Graph:
+    """One graph running the given solve graphs concurrently (one launch)."""
+    arr = (ctypes.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+    h = ctypes.c_void_p()
+    _check(load().csgd_graph_batch_create(arr, len(graphs), ctypes.byref(h)))
+    return Graph(h, list(graphs))
 
 
 def solver_create(part: Partition, params: dict, y, stream=None) -> Solver:

@@ -293,7 +293,7 @@ int64_t bp_partials_per_slot(const csgd_partition* P) {
     return std::max<int64_t>(1, (P->p.max_tile_voxels + 255) / 256);
 }
 
-int solver_reset_state(csgd_solver* S, cudaStream_t s) {
+int solver_reset_device(csgd_solver* S, cudaStream_t s) {
     const SolverBuffers& b = S->sb;
     CSGD_CUDA(cudaMemcpyAsync(b.r, b.y, sizeof(float) * S->n_rays, cudaMemcpyDeviceToDevice, s),
               "r = y");
@@ -307,11 +307,21 @@ int solver_reset_state(csgd_solver* S, cudaStream_t s) {
     CSGD_CUDA(cudaMemsetAsync(b.counters, 0, sizeof(unsigned) * b.max_slots, s), "counters");
     CSGD_CUDA(cudaMemsetAsync(b.nnz_slot, 0, sizeof(unsigned long long) * b.max_slots, s),
               "slot counters");
+    return CSGD_OK;
+}
+
+void solver_reset_host(csgd_solver* S) {
     S->rng = SplitMix64(S->prm.seed);
     S->epoch = 0;
     S->steps_done = 0;
     S->queue.clear();
     S->epoch_open = false;
+}
+
+int solver_reset_state(csgd_solver* S, cudaStream_t s) {
+    int rc = solver_reset_device(S, s);
+    if (rc) return rc;
+    solver_reset_host(S);
     return CSGD_OK;
 }
 
@@ -407,8 +417,9 @@ int take_events(csgd_solver* S, int n, int* first) {
     return CSGD_OK;
 }
 
-int execute_plan(csgd_solver* S, Plan& pl, cudaStream_t s) {
-    const Partition& p = S->P->p;
+// Device buffers for a plan: capacity, history and the upload of its items and
+// step descriptors (stream-ordered).
+int prepare_plan(csgd_solver* S, Plan& pl, cudaStream_t s) {
     if (pl.ops.empty()) return CSGD_OK;
     int rc = ensure_sched_capacity(S, (int64_t)pl.items.size(), (int64_t)pl.steps.size(), s);
     if (rc) return rc;
@@ -420,6 +431,13 @@ int execute_plan(csgd_solver* S, Plan& pl, cudaStream_t s) {
     if (!pl.steps.empty())
         CSGD_CUDA(cudaMemcpyAsync(S->d_steps, pl.steps.data(), sizeof(StepDesc) * pl.steps.size(),
                                   cudaMemcpyHostToDevice, s), "upload steps");
+    return CSGD_OK;
+}
+
+// The kernel launches of a prepared plan (no allocation, no host sync:
+// capturable into a CUDA graph).
+int launch_plan(csgd_solver* S, Plan& pl, cudaStream_t s) {
+    const Partition& p = S->P->p;
     for (const auto& op : pl.ops) {
         if (op.n < 0) {
             int e0 = 0;
@@ -461,6 +479,13 @@ int execute_plan(csgd_solver* S, Plan& pl, cudaStream_t s) {
                                S->P->sm_count, s, S->profiling ? evs : nullptr), "batch kernels");
     }
     return CSGD_OK;
+}
+
+int execute_plan(csgd_solver* S, Plan& pl, cudaStream_t s) {
+    if (pl.ops.empty()) return CSGD_OK;
+    int rc = prepare_plan(S, pl, s);
+    if (rc) return rc;
+    return launch_plan(S, pl, s);
 }
 
 // Append the next `n` scheduled steps (and the epoch closes they cross) to pl.
@@ -1018,6 +1043,126 @@ int32_t csgd_solver_history(csgd_solver* S, csgd_step_info* out, int64_t capacit
         out[k].mu = row[3];
         out[k].nnz = (int64_t)row[4];
     }
+    return CSGD_OK;
+}
+
+struct csgd_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+int32_t csgd_solver_graph_create(csgd_solver* S, int64_t n_steps, float* x_out, int32_t x_on_host,
+                                 csgd_graph** out) {
+    if (!S || !out || n_steps < 0) return fail(CSGD_ERR_INVALID_ARG, "bad argument");
+    *out = nullptr;
+    if (S->profiling) return fail(CSGD_ERR_STATE, "disable profiling before building a graph");
+    const Partition& p = S->P->p;
+    if (x_out && x_on_host) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, x_out) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            return fail(CSGD_ERR_INVALID_ARG, "a graph can copy x only to pinned host memory");
+        }
+    }
+    cudaStream_t cs = nullptr;
+    CSGD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
+    // plan the whole run from a fresh schedule and upload it before capturing
+    solver_reset_host(S);
+    Plan pl;
+    plan_scheduled(S, &pl, n_steps, true);
+    int rc = prepare_plan(S, pl, cs);
+    if (rc == CSGD_OK && x_out && x_on_host && !S->d_xrow)
+        rc = dmalloc(S, (void**)&S->d_xrow, sizeof(float) * S->n_vox, "cudaMalloc(x row)");
+    if (rc == CSGD_OK) {
+        cudaError_t e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) rc = cuda_fail(e, "upload sync");
+    }
+    cudaGraph_t graph = nullptr;
+    if (rc == CSGD_OK) {
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) rc = cuda_fail(e, "begin capture");
+    }
+    if (rc == CSGD_OK) {
+        rc = solver_reset_device(S, cs);
+        if (rc == CSGD_OK) rc = launch_plan(S, pl, cs);
+        if (rc == CSGD_OK && x_out) {
+            float* dst = x_on_host ? S->d_xrow : x_out;
+            cudaError_t e = launch_tile_to_rowmajor(p.dg, S->sb.x, dst, p.max_tile_voxels, cs);
+            if (e == cudaSuccess && x_on_host)
+                e = cudaMemcpyAsync(x_out, S->d_xrow, sizeof(float) * S->n_vox,
+                                    cudaMemcpyDeviceToHost, cs);
+            if (e != cudaSuccess) rc = cuda_fail(e, "x output");
+        }
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (rc == CSGD_OK && e != cudaSuccess) rc = cuda_fail(e, "end capture");
+    }
+    cudaStreamDestroy(cs);
+    // the graph starts from the seed each time it runs; so does the host side
+    solver_reset_host(S);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    csgd_graph* G = new (std::nothrow) csgd_graph;
+    if (!G) {
+        cudaGraphDestroy(graph);
+        return fail(CSGD_ERR_OOM, "host allocation");
+    }
+    G->graph = graph;
+    cudaError_t e = cudaGraphInstantiate(&G->exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        delete G;
+        return cuda_fail(e, "graph instantiate");
+    }
+    *out = G;
+    return CSGD_OK;
+}
+
+int32_t csgd_graph_batch_create(csgd_graph* const* parts, int32_t n, csgd_graph** out) {
+    if (!parts || n < 1 || !out) return fail(CSGD_ERR_INVALID_ARG, "bad argument");
+    *out = nullptr;
+    cudaGraph_t g = nullptr;
+    CSGD_CUDA(cudaGraphCreate(&g, 0), "cudaGraphCreate");
+    for (int k = 0; k < n; ++k) {
+        if (!parts[k] || !parts[k]->graph) {
+            cudaGraphDestroy(g);
+            return fail(CSGD_ERR_INVALID_ARG, "NULL part");
+        }
+        cudaGraphNode_t node;
+        cudaError_t e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, parts[k]->graph);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_fail(e, "add child graph");
+        }
+    }
+    csgd_graph* G = new (std::nothrow) csgd_graph;
+    if (!G) {
+        cudaGraphDestroy(g);
+        return fail(CSGD_ERR_OOM, "host allocation");
+    }
+    G->graph = g;
+    cudaError_t e = cudaGraphInstantiate(&G->exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        delete G;
+        return cuda_fail(e, "graph instantiate");
+    }
+    *out = G;
+    return CSGD_OK;
+}
+
+int32_t csgd_graph_launch(csgd_graph* G, csgd_stream stream) {
+    if (!G || !G->exec) return fail(CSGD_ERR_INVALID_ARG, "NULL graph");
+    CSGD_CUDA(cudaGraphLaunch(G->exec, (cudaStream_t)stream), "cudaGraphLaunch");
+    return CSGD_OK;
+}
+
+int32_t csgd_graph_destroy(csgd_graph* G) {
+    if (!G) return CSGD_OK;
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    delete G;
     return CSGD_OK;
 }
 

@@ -144,3 +144,32 @@ def random_sphere_poses(n_views: int, radius: float, sdd: float, seed: int) -> n
 
 
 ALL = {"parallel2d_64": parallel2d_64, "fan2d_512": fan2d_512, "cone3d_256": cone3d_256}
+
+
+def batch_fan2d(n_problems: int = 64, seed: int = 1709 + 3, n_range=(128, 1024),
+                views_range=(60, 900), epochs: int = 3) -> list:
+    """Many independent 2D fan-beam problems of seeded, uneven sizes (sparse-view
+    included): n ~ U[128, 1024] pixels per side, views ~ U[60, 900], curved detector
+    covering the circumscribed circle with 1.5 n bins, source at 2 n; 8 view blocks x
+    4 x 4 tiles, density-weighted choice (alpha 0.5, b 8); a fixed number of epochs."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(n_problems):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        views = int(rng.integers(views_range[0], views_range[1] + 1))
+        nu = int(math.ceil(1.5 * n))
+        sod = 2.0 * n
+        half_fan = math.asin(math.sqrt(2.0) * (n / 2) / sod)
+        vb = min(8, views)
+        out.append(dict(
+            name="batch_fan2d_%02d_%d_%dx%d" % (k, n, views, nu),
+            geom=dict(kind="fan2d_curved", n=(n, n), h=1.0, angles=_angles(views, 360.0), nu=nu,
+                      nv=1, pu=2.0 * half_fan / nu, pv=1.0, sod=sod, sdd=2.0 * sod),
+            part=dict(tiles=(4, 4), view_blocks=vb, det_blocks=(1, 1)),
+            solver=dict(sampling=2, alpha=0.5, gamma=1.0, b=float(vb), group_size=1, sync=0,
+                        seed=SCHED_SEED + 100 + k, theta_step=1.0 / 40.0),
+            phantom=dict(n_shapes=12, seed=1709 + 200 + k),
+            noise=dict(kind="poisson", level=1e5, seed=1709 + 300 + k),
+            steps=epochs * 16 * int(math.ceil(0.5 * vb)),
+        ))
+    return out

@@ -1,0 +1,77 @@
+"""Batched solves (one CUDA-graph launch for many problems) against solo solves (GPU).
+
+The batched and the one-by-one paths run the same deterministic kernels on
+independent state, so every problem's reconstruction must be identical.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from synth import configs as C  # noqa: E402
+from synth import data as D  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_00953_gb300 import build as B
+    B.build()
+    from paper_1709_00953_gb300 import batch, csgd
+    return csgd, batch
+
+
+def _problems(batch, k=6):
+    cfgs = C.batch_fan2d(n_problems=k, n_range=(64, 160), views_range=(30, 120), epochs=2,
+                         seed=42)
+    return [batch.Problem(c, D.make_data(c)[0]) for c in cfgs]
+
+
+def test_graph_solve_equals_plain_solve(mods):
+    csgd, batch = mods
+    (p,) = _problems(batch, 1)
+    g = p.graph()
+    g.launch()
+    torch.cuda.synchronize()
+    x_graph = p.x.clone()
+    p.x.zero_()
+    p.solve_plain()
+    torch.cuda.synchronize()
+    assert torch.equal(p.x, x_graph)
+    # a second launch repeats the same solve
+    p.x.zero_()
+    g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(p.x, x_graph)
+
+
+def test_batch_equals_one_by_one(mods):
+    csgd, batch = mods
+    probs = _problems(batch, 6)
+    b = batch.Batch(probs)
+    b.launch()
+    torch.cuda.synchronize()
+    xs = [p.x.clone() for p in probs]
+    for p in probs:
+        p.x.fill_(-1.0)
+    b.solve_one_by_one()
+    for p, xb in zip(probs, xs):
+        assert torch.equal(p.x, xb), p.cfg["name"]
+        assert float(p.x.abs().max()) > 0
+
+
+def test_graph_to_pinned_host(mods):
+    csgd, batch = mods
+    (p,) = _problems(batch, 1)
+    host = torch.empty(p.partition.n_voxels, dtype=torch.float32).pin_memory()
+    g = p.solver.graph(p.steps, host)
+    g.launch()
+    torch.cuda.synchronize()
+    p.solve_plain()
+    torch.cuda.synchronize()
+    assert torch.equal(host, p.x.cpu())
+    with pytest.raises(csgd.CsgdError):
+        p.solver.graph(p.steps, torch.empty(p.partition.n_voxels, dtype=torch.float32))

@@ -77,6 +77,10 @@ CASES = {
     "fan_flat_ragged": C.small_fan2d(n=80, views=40, nu=120, tiles=(2, 3), vb=4, du=3,
                                      curved=False),
     "cone_ragged": C.small_cone3d(n=24, views=12, nd=40, tiles=(2, 2, 3), du=2, dv=2),
+    "custom_sphere": dict(
+        C.small_cone3d(n=20, views=10, nd=36, tiles=(2, 3, 2), du=1, dv=2),
+        geom=dict(kind="custom3d", n=(20, 20, 20), h=1.0, nu=36, nv=36, pu=1.8, pv=1.8,
+                  poses=C.random_sphere_poses(10, 40.0, 80.0, seed=9))),
 }
 
 
@@ -182,7 +186,8 @@ def _solver_pair(csgd, cfg, steps):
 
 
 @pytest.mark.parametrize("name,steps", [("parallel64", 400), ("fan_curved_ragged", 60),
-                                        ("fan_flat_ragged", 40), ("cone_ragged", 30)])
+                                        ("fan_flat_ragged", 40), ("cone_ragged", 30),
+                                        ("custom_sphere", 24)])
 def test_solver_parity(csgd, name, steps):
     cfg = CASES[name]
     x_gpu, x_ref, hist, o, rep, y = _solver_pair(csgd, cfg, steps)
