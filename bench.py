@@ -65,7 +65,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="fan2d_512", choices=sorted(C.ALL) + ["batch_fan64"])
+    ap.add_argument("--workload", default="fan2d_512", choices=sorted(C.ALL) + ["batch_fan64", "serve"])
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second")
+    ap.add_argument("--jobs", type=int, default=40, help="serve: number of requests")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -442,11 +444,56 @@ def run_batch(args, world, rank, local):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# serving workload: Poisson arrivals of mixed fan / cone jobs, continuous batching
+# ---------------------------------------------------------------------------
+def run_serve(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local if world > 1 else 0)
+    import __graft_entry__ as GE
+    GE.build()
+    from paper_1709_00953_gb300 import serve
+    cfgs = C.serving_jobs(n_jobs=args.jobs)
+    ys = [D.make_data(c, device="cuda")[0] for c in cfgs]
+    budget = 40 << 30
+    # warm-up: a few jobs served back to back
+    warm = [serve.Job(c, y, 0.0, c["name"]) for c, y in list(zip(cfgs, ys))[:max(1, args.warmup)]]
+    serve.Server(budget).run(warm)
+    arrivals = serve.poisson_arrivals(len(cfgs), args.rate, seed=1709 + 4)
+    jobs = [serve.Job(c, y, float(a), c["name"]) for c, y, a in zip(cfgs, ys, arrivals)]
+    srv = serve.Server(budget, max_running=16)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    t0 = time.perf_counter()
+    srv.run(jobs)
+    wall = time.perf_counter() - t0
+    ck = clocks.stop()
+    s = serve.summary(jobs, wall)
+    line = {
+        "metric": "solves/s with p50/p99 latency (Poisson arrivals, continuous batching)",
+        "value": s["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": len(jobs),
+        "warmup": args.warmup, "ms_per_step": 1e3 * wall / len(jobs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serve", "jobs": len(jobs), "rate_per_s": args.rate,
+                   "mix": "fan 256^2-1024^2, cone 64^3-128^3, 1 in 8 a 100^3 / 4.2M-ray cone",
+                   "hbm_budget_gb": budget / 2 ** 30},
+        "latency": {"p50_s": s["p50_latency_s"], "p99_s": s["p99_latency_s"],
+                    "mean_s": s["mean_latency_s"]},
+        "max_concurrency": srv.max_concurrency, "wall_s": wall,
+    }
+    if ck:
+        line["clocks"] = ck
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
     if args.workload == "batch_fan64":
         return run_batch(args, world, rank, local)
+    if args.workload == "serve":
+        return run_serve(args, world, rank, local)
     cfg = C.ALL[args.workload]()
     if args.impl == "reference":
         return run_reference(args, cfg, world, rank)

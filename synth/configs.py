@@ -173,3 +173,52 @@ def batch_fan2d(n_problems: int = 64, seed: int = 1709 + 3, n_range=(128, 1024),
             steps=epochs * 16 * int(math.ceil(0.5 * vb)),
         ))
     return out
+
+
+def cone3d_job(n: int, views: int, nd: int, tiles=(2, 2, 2), group: int = 30, epochs: int = 1,
+               seed: int = 0, name: str = "") -> dict:
+    """A circular cone-beam job: n^3 voxels, `views` views of nd^2 pixels at a pitch
+    that covers the volume (SOD 2n, SDD 4n), single-view row blocks in groups."""
+    pitch = 2.0 * 1.5 * n / nd
+    groups = int(math.ceil(views / group))
+    n_tiles = tiles[0] * tiles[1] * tiles[2]
+    return dict(
+        name=name or "cone3d_%d_%dx%d" % (n, views, nd),
+        geom=dict(kind="cone3d", n=(n, n, n), h=1.0, angles=_angles(views, 360.0), nu=nd, nv=nd,
+                  pu=pitch, pv=pitch, sod=2.0 * n, sdd=4.0 * n),
+        part=dict(tiles=tiles, view_blocks=views, det_blocks=(1, 1)),
+        solver=dict(sampling=2, alpha=1.0, gamma=1.0, b=1.0, group_size=group, sync=0,
+                    seed=SCHED_SEED + 500 + seed, theta_step=1.0 / 40.0),
+        phantom=dict(n_shapes=10, seed=1709 + 500 + seed),
+        noise=dict(kind="poisson", level=1e4, seed=1709 + 600 + seed),
+        steps=epochs * groups * n_tiles,
+    )
+
+
+def serving_jobs(n_jobs: int = 40, seed: int = 1709 + 4, small: bool = False) -> list:
+    """A seeded mix of reconstruction requests: 2D fan beams of 256^2 .. 1024^2 (or
+    64^2 .. 128^2 when small) and 3D cone beams of 64^3 .. 128^3 (24^3 .. 32^3 when
+    small), one in eight a 100^3-volume job with 360 views of 108^2 pixels (~4.2M
+    rays, the paper's "a million unknowns, four million measurements" scale)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(n_jobs):
+        kind = rng.random()
+        if kind < 0.5:
+            lo, hi = (64, 128) if small else (256, 1024)
+            n = int(rng.integers(lo, hi + 1))
+            views = int(rng.integers(60, 360 if small else 720))
+            cfg = batch_fan2d(1, seed=seed * 1000 + k, n_range=(n, n), views_range=(views, views),
+                              epochs=2)[0]
+            cfg["name"] = "serve_fan2d_%02d_%d_%d" % (k, n, views)
+        elif kind < 0.875 or small:
+            lo, hi = (24, 32) if small else (64, 128)
+            n = int(rng.integers(lo, hi + 1))
+            views = int(rng.integers(24, 60 if small else 180))
+            nd = int(1.5 * n)
+            cfg = cone3d_job(n, views, nd, group=min(10, views), seed=k,
+                             name="serve_cone3d_%02d_%d_%d" % (k, n, views))
+        else:
+            cfg = cone3d_job(100, 360, 108, group=30, seed=k, name="serve_cone3d_%02d_100_4M" % k)
+        out.append(cfg)
+    return out

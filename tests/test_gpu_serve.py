@@ -1,0 +1,71 @@
+"""Serving: jobs arriving over time, continuously batched, against solo solves (GPU).
+
+Each job's result must be identical when it runs alone and when it runs in the
+mix; the HBM budget must bound how many jobs run at once.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from synth import configs as C  # noqa: E402
+from synth import data as D  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_00953_gb300 import build as B
+    B.build()
+    from paper_1709_00953_gb300 import csgd, serve
+    return csgd, serve
+
+
+def _jobs(serve, n=8):
+    cfgs = C.serving_jobs(n_jobs=n, seed=77, small=True)
+    arrivals = serve.poisson_arrivals(n, rate_per_s=200.0, seed=5)
+    return [serve.Job(c, D.make_data(c)[0], float(a), c["name"]) for c, a in zip(cfgs, arrivals)]
+
+
+def _solo(csgd, job):
+    g = csgd.Geometry(job.cfg["geom"])
+    p = csgd.Partition(g, **job.cfg["part"])
+    s = csgd.Solver(p, job.cfg["solver"], torch.tensor(job.y, device="cuda"))
+    x = torch.zeros(p.n_voxels, dtype=torch.float32, device="cuda")
+    s.solve(job.cfg["steps"], x, report=False)
+    torch.cuda.synchronize()
+    return x.cpu().numpy()
+
+
+def test_served_results_equal_solo_results(mods):
+    csgd, serve = mods
+    jobs = _jobs(serve)
+    srv = serve.Server(hbm_budget_bytes=8 << 30, max_running=8)
+    srv.run(jobs)
+    assert srv.max_concurrency >= 2  # jobs did overlap
+    for j in jobs:
+        assert j.done > 0 and j.latency > 0
+        np.testing.assert_array_equal(j.x, _solo(csgd, j), err_msg=j.name)
+    s = serve.summary(jobs, max(j.done for j in jobs))
+    assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
+
+
+def test_budget_bounds_concurrency(mods):
+    csgd, serve = mods
+    jobs = _jobs(serve, 5)
+    biggest = max(serve.job_footprint(j.cfg) for j in jobs)
+    srv = serve.Server(hbm_budget_bytes=biggest, max_running=8)
+    for j in jobs:
+        j.arrival = 0.0
+    srv.run(jobs)
+    # admission never lets the running jobs' footprints exceed the budget
+    assert 0 < srv.max_used <= biggest
+    assert srv.max_concurrency < len(jobs)
+    for j in jobs:
+        assert j.x is not None
+    too_small = serve.Server(hbm_budget_bytes=biggest // 4, max_running=2)
+    with pytest.raises(ValueError):
+        too_small.run(_jobs(serve, 5))
