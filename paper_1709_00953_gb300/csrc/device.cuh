@@ -153,30 +153,33 @@ __device__ __forceinline__ int walk(const float q[3], const float inv[3], const 
     float tc = tin;
     int cnt = 0;
     if (DIM == 2) {
+        // branch-free advance: lanes of a warp that step along different axes
+        // execute the same instructions
         float tx = tn[0], ty = tn[1];
         int ix = i[0], iy = i[1];
         float px = pl[0], py = pl[1];
+        const int sx = st[0], sy = st[1];
+        const int dsx = sx * b.stride[0], dsy = sy * b.stride[1];
+        const float fsx = (float)sx, fsy = (float)sy;
+        const unsigned nx = (unsigned)b.n[0], ny = (unsigned)b.n[1];
         for (;;) {
-            bool bx = tx <= ty;
-            float t = fminf(bx ? tx : ty, tout);
-            float len = fmaxf(t - tc, 0.f);
+            const bool bx = tx <= ty;
+            const float t = fminf(bx ? tx : ty, tout);
+            const float len = fmaxf(t - tc, 0.f);
             f(idx, len);
             cnt += len > 0.f;
             if (t >= tout) break;
             tc = t;
-            if (bx) {
-                ix += st[0];
-                if ((unsigned)ix >= (unsigned)b.n[0]) break;
-                idx += st[0] * b.stride[0];
-                px += (float)st[0];
-                tx = (px - q[0]) * inv[0];
-            } else {
-                iy += st[1];
-                if ((unsigned)iy >= (unsigned)b.n[1]) break;
-                idx += st[1] * b.stride[1];
-                py += (float)st[1];
-                ty = (py - q[1]) * inv[1];
-            }
+            ix += bx ? sx : 0;
+            iy += bx ? 0 : sy;
+            idx += bx ? dsx : dsy;
+            px += bx ? fsx : 0.f;
+            py += bx ? 0.f : fsy;
+            const float nxt = (px - q[0]) * inv[0];
+            const float nyt = (py - q[1]) * inv[1];
+            tx = bx ? nxt : tx;
+            ty = bx ? ty : nyt;
+            if ((unsigned)ix >= nx || (unsigned)iy >= ny) break;
         }
     } else {
         float tx = tn[0], ty = tn[1], tz = tn[2];
