@@ -39,13 +39,15 @@ from synth import data as D  # noqa: E402
 #   dual forward: length (1) + two multiply-adds (2 x 2)                          = 5
 ALG_FLOP = {"backproject": 6.0, "forward_dual": 8.0}
 FP32_LANES_PER_SM = 128
+# enough solves for a timed region of about 1.5 s (several clock samples)
+DEFAULT_STEPS = {"fan2d_512": 250, "parallel2d_64": 250, "cone3d_256": 12, "batch_fan64": 20}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of
 # the fan2d_512 workload (profiles/fan2d_512_kernels_ncu.md), valid only for the
 # kernel sources they were taken from (hash of ops.cu, device.cuh, common.h).
 NCU_TRAFFIC = {
-    ("fan2d_512_720x768_8x16_importance", "96171a63424e9d9d"): {
-        "backproject": 2078976 + 512, "forward_dual": 2330880},
+    ("fan2d_512_720x768_8x16_importance", "4563d5448771ca71"): {
+        "backproject": 2145792 + 1024, "forward_dual": 2526720},
 }
 KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/csrc/device.cuh",
                   "paper_1709_00953_gb300/csrc/common.h")
@@ -62,7 +64,8 @@ def kernel_hash() -> str:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 250 solves of fan2d_512, fewer for the larger workloads)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="fan2d_512", choices=sorted(C.ALL) + ["batch_fan64", "serve"])
@@ -71,7 +74,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = DEFAULT_STEPS.get(a.workload, 20)
+    return a
 
 
 def dist_env():
@@ -255,32 +261,40 @@ def run_gpu(args, cfg, world, rank, local):
     torch.cuda.synchronize()
 
     # ---- device-timed region: inputs resident, L2 flushed before every step ----
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    clocks = ClockSampler(torch.cuda.current_device())
-    solver.profile(True)
-    solver.profile_read(reset=True)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    t_wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        one_solve()
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter() - t_wall0
-    ck = clocks.stop()
-    prof = solver.profile_read(reset=True)
-    solver.profile(False)
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        ms = float(t.item())
+    def timed(instrumented: bool):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        clocks = ClockSampler(torch.cuda.current_device())
+        solver.profile(instrumented)
+        solver.profile_read(reset=True)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            one_solve()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ck = clocks.stop()
+        prof = solver.profile_read(reset=True)
+        solver.profile(False)
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            torch.distributed.barrier()
+            ms = float(t.item())
+        return ms, wall, ck, prof
+
+    # the headline: no per-kernel events in the stream
+    ms, t_wall, ck, _ = timed(False)
+    # the same K solves again with CUDA events around every launch, on the
+    # solver's stream: per-kernel durations for the roofline and the shares
+    ms_instr, _, _, prof = timed(True)
     updates = 3.0 * nnz_per_solve * args.steps * world
     value = updates / (ms / 1e3)
 
@@ -358,6 +372,8 @@ def run_gpu(args, cfg, world, rank, local):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "solves_per_s": 1e3 * args.steps * world / ms},
         "roofline": roof, "kernels": kernels, "gpu_launches": launches,
+        "kernel_timing": "per-launch CUDA events in a second pass of the same %d solves "
+                         "(%.3f ms per solve with the events)" % (args.steps, ms_instr / args.steps),
         "wall_s_timed": t_wall,
     }
     if ck:
