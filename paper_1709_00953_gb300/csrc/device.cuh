@@ -57,32 +57,6 @@ __device__ __forceinline__ void ray_setup(const DevGeom& G, const DevView& V, co
     for (int a = 0; a < 3; ++a) d[a] *= inv;
 }
 
-// Continuous detector bin coordinate of a point P (voxel units, grid-centred).
-__device__ __forceinline__ void detector_coord(const DevGeom& G, const DevView& V, const float P[3],
-                                               float* wu, float* wv) {
-    if (G.kind == PARALLEL_2D) {
-        *wu = (P[0] * V.eu[0] + P[1] * V.eu[1]) / G.pu + 0.5f * G.nu;
-        *wv = 0.5f;
-        return;
-    }
-    float r0 = P[0] - V.S[0], r1 = P[1] - V.S[1], r2 = P[2] - V.S[2];
-    float depth = r0 * V.dc[0] + r1 * V.dc[1] + r2 * V.dc[2];
-    float lu = r0 * V.eu[0] + r1 * V.eu[1] + r2 * V.eu[2];
-    if (G.kind == FAN_2D_CURVED) {
-        *wu = atan2f(lu, depth) / G.pu + 0.5f * G.nu;
-        *wv = 0.5f;
-        return;
-    }
-    float lam = V.sdd / depth;
-    *wu = lam * lu / G.pu + 0.5f * G.nu;
-    if (G.dim == 3) {
-        float lv = r0 * V.ev[0] + r1 * V.ev[1] + r2 * V.ev[2];
-        *wv = lam * lv / G.pv + 0.5f * G.nv;
-    } else {
-        *wv = 0.5f;
-    }
-}
-
 // Box of voxels for a traversal: tile-centred lower corner, size, index strides.
 struct Box {
     float lo[3];
@@ -227,19 +201,39 @@ __device__ __forceinline__ int traverse(const float q[3], const float inv[3], co
     return walk<DIM>(q, inv, b, tin, tout, f);
 }
 
+// Reciprocal by the hardware approximation (rcp.approx: relative error about
+// 1e-7); used only where a result picks candidate bins under a margin.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// atan x by its Taylor series to x^11: error below |x|^13 / 13 < 1e-5 rad on
+// |x| <= 0.5 (the alternating series' first dropped term).
+__device__ __forceinline__ float atan_series(float x) {
+    const float x2 = x * x;
+    float p = fmaf(x2, -1.0f / 11.0f, 1.0f / 9.0f);
+    p = fmaf(x2, p, -1.0f / 7.0f);
+    p = fmaf(x2, p, 1.0f / 5.0f);
+    p = fmaf(x2, p, -1.0f / 3.0f);
+    p = fmaf(x2, p, 1.0f);
+    return x * p;
+}
+
 // Bin coordinates (wu, wv) of a voxel centre P and the half-widths (hu, hv) of
 // the voxel's shadow, for choosing the candidate bins of a voxel: the shadow of
 // the unit voxel is [w - h1, w + h1] to first order, h1 = 0.5 sum_k |dw/dP_k|;
 // the second derivative of a perspective or angular map is at most ~2 |grad w|
 // / depth, so over half a voxel diagonal (|delta|^2 <= 3/4) the second-order
 // term is below 0.75 |grad w| / depth <= 1.5 h1 / depth: h = h1 (1 + 1.5 /
-// depth).  Callers add a small margin for rounding.  Uses a correctly
-// rounded reciprocal instead of divisions and, when the curved detector spans
-// |gamma| < 0.46 rad, atan by its Taylor series to x^11 (error below
-// |x|^13 / 13 < 1e-5 rad on |x| <= 0.5).
+// depth).  Callers add a small margin for rounding, the approximate
+// reciprocals and, when the curved detector spans |gamma| < 0.46 rad, the
+// series atan.
+template <int DIM>
 __device__ __forceinline__ void voxel_shadow(const DevGeom& G, const DevView& V, const float P[3],
                                              float* wu, float* wv, float* hu, float* hv) {
-    if (G.kind == PARALLEL_2D) {
+    if (DIM == 2 && G.kind == PARALLEL_2D) {
         *wu = fmaf(P[0] * V.eu[0] + P[1] * V.eu[1], G.inv_pu, 0.5f * G.nu);
         *hu = 0.5f * (fabsf(V.eu[0]) + fabsf(V.eu[1])) * G.inv_pu;
         *wv = 0.5f;
@@ -249,24 +243,12 @@ __device__ __forceinline__ void voxel_shadow(const DevGeom& G, const DevView& V,
     float r0 = P[0] - V.S[0], r1 = P[1] - V.S[1], r2 = P[2] - V.S[2];
     float depth = r0 * V.dc[0] + r1 * V.dc[1] + r2 * V.dc[2];
     float lu = r0 * V.eu[0] + r1 * V.eu[1] + r2 * V.eu[2];
-    float rd = __frcp_rn(depth);
-    if (G.kind == FAN_2D_CURVED) {
-        float x = lu * rd;  // tan(gamma)
-        float gam;
-        if (G.fast_arc) {
-            float x2 = x * x;
-            float p = fmaf(x2, -1.0f / 11.0f, 1.0f / 9.0f);
-            p = fmaf(x2, p, -1.0f / 7.0f);
-            p = fmaf(x2, p, 1.0f / 5.0f);
-            p = fmaf(x2, p, -1.0f / 3.0f);
-            p = fmaf(x2, p, 1.0f);
-            gam = x * p;
-        } else {
-            gam = atan2f(lu, depth);
-        }
+    float rd = rcp_approx(depth);
+    if (DIM == 2 && G.kind == FAN_2D_CURVED) {
+        float gam = G.fast_arc ? atan_series(lu * rd) : atan2f(lu, depth);
         *wu = fmaf(gam, G.inv_pu, 0.5f * G.nu);
         // d gamma / dP = (depth e_u - lu d_c) / (depth^2 + lu^2)
-        float sc = 0.5f * G.inv_pu * __frcp_rn(fmaf(depth, depth, lu * lu));
+        float sc = 0.5f * G.inv_pu * rcp_approx(fmaf(depth, depth, lu * lu));
         *hu = sc * (fabsf(depth * V.eu[0] - lu * V.dc[0]) + fabsf(depth * V.eu[1] - lu * V.dc[1])) *
               fmaf(1.5f, rd, 1.0f);
         *wv = 0.5f;
@@ -278,7 +260,7 @@ __device__ __forceinline__ void voxel_shadow(const DevGeom& G, const DevView& V,
     *wu = fmaf(lam * lu, G.inv_pu, 0.5f * G.nu);
     float sc = 0.5f * lam * rd * fmaf(1.5f, rd, 1.0f);
     float hu_ = fabsf(depth * V.eu[0] - lu * V.dc[0]) + fabsf(depth * V.eu[1] - lu * V.dc[1]);
-    if (G.dim == 3) {
+    if (DIM == 3) {
         float lv = r0 * V.ev[0] + r1 * V.ev[1] + r2 * V.ev[2];
         *wv = fmaf(lam * lv, G.inv_pv, 0.5f * G.nv);
         hu_ += fabsf(depth * V.eu[2] - lu * V.dc[2]);

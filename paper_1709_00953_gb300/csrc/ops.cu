@@ -3,10 +3,13 @@
 //   k_forward      z_I = A_I^J x_J (one vector) or, in the solver, p = A x_J and
 //                  q = A g_J in one traversal with ||q||^2 in FP64 and the step
 //                  length mu computed by the last CTA (Alg. 1, Eq. 'step').
-//   k_backproject  g_J = (A_I^J)^T r_I (Eq. 'direction'): ray-driven traversal of a
-//                  shared-memory sub-box of the tile, partial sums reduced across
-//                  the CTAs of a thread-block cluster through distributed shared
-//                  memory, g^T g in FP64.  No global atomics.
+//   k_ray_table    per launch, the line (tile-centred point q, 1/d) and the
+//                  residual r of every ray of every slot, set up once.
+//   k_backproject  g_J = (A_I^J)^T r_I (Eq. 'direction'): voxel-driven gather over
+//                  the ray table (each voxel sums len * r over the bins of its
+//                  shadow), partial sums of the view chunks reduced across the
+//                  CTAs of a thread-block cluster through distributed shared
+//                  memory, g^T g in FP64.  No atomics.
 //   k_epilogue     z_I^j = p + mu q, r -= z_new - z_old (the refresh of Alg. 2-4
 //                  applied incrementally), x^_J += x_J + mu g_J.
 //   k_average      x_J = x^_J / count_J at the end of an epoch.
@@ -239,6 +242,7 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
     const DevGeom& G = a.G;
     const DevView V = G.views[it.view];
     const DevVT E = G.vt[(int64_t)it.view * G.n_tiles + a.j];
+    const DevTile& tile = G.tiles[a.j];
     const int wu = it.u1 - it.u0;
     const int nr = wu * (it.v1 - it.v0);
     RayRec* dst = a.table + (int64_t)it.slot * a.slot_stride + it.ray_off;
@@ -248,6 +252,17 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
         float q[3], d[3], inv[3];
         ray_setup(G, V, E, ku, kv, q, d);
         reciprocal(d, inv);
+        // A ray parallel to axis ax whose q_ax lies exactly on a voxel face moves
+        // one ulp up: it meets the same voxels (a face belongs to the voxel above
+        // it, for the walk as for the oracle) and (face - q_ax) / d_ax is never 0 / 0.
+#pragma unroll
+        for (int ax = 0; ax < DIM; ++ax) {
+            if (isinf(inv[ax])) {
+                const float hn = 0.5f * (float)tile.n[ax];
+                const float face = (float)__float2int_rn(q[ax] + hn) - hn;
+                if (q[ax] == face) q[ax] = nextafterf(q[ax], INFINITY);
+            }
+        }
         const int64_t ray = ray_index(G, it.view, ku, kv);
         *reinterpret_cast<float4*>(dst[k].a) = make_float4(q[0], q[1], inv[0], inv[1]);
         *reinterpret_cast<float4*>(dst[k].b) =
@@ -285,30 +300,190 @@ struct BPArgs {
 
 // g_J = (A_I^J)^T r_I, voxel-driven: a thread owns one voxel of the tile and,
 // for every view of its chunk, sums len * r over the rays whose bins lie within
-// the voxel's shadow (half-width hw around the bin of the voxel's centre).  The
-// length is the voxel's slab clip of the ray, t = (plane - q) / d on each face,
-// i.e. the very crossings the forward walk evaluates, so forward and adjoint use
-// the same lengths.  No atomics: the C CTAs of a cluster (one per view chunk)
-// add their partial sums through distributed shared memory in a fixed order.
-// Per-view data of a backprojection CTA, staged in shared memory.
-struct ViewCtx {
+// the voxel's shadow.  The length is the voxel's slab clip of the ray, t =
+// (plane - q) / d on each face, i.e. the very crossings the forward walk
+// evaluates, so forward and adjoint use the same lengths.  The ray table never
+// holds a ray parallel to an axis whose q lies exactly on a face of that axis
+// (see ray_table_item), so no crossing is 0 * inf and the clip needs no special
+// case: a parallel ray's crossings are +-inf, which constrain nothing when q is
+// inside the slab and empty the interval when it is outside.  No atomics: the C
+// CTAs of a cluster (one per view chunk) add their partial sums through
+// distributed shared memory in a fixed order.
+
+// bins added on each side of a voxel's shadow window: covers the series atan
+// (below 0.011 bin at the finest pitch used), the approximate reciprocals
+// (relative error ~1e-7) and FP32 rounding
+constexpr float kShadowMargin = 0.02f;
+constexpr int kViewBatch = 96;
+
+// Per-view data of a 2D backprojection CTA, staged in shared memory.  For voxel
+// (i0, i1) of the tile, r = P - S = (R0 + i0, R1 + i1); its depth along the
+// central ray is r . d_c and its lateral offset r . e_u with e_u = (d_c1, -d_c0)
+// (the 2D detector frame is d_c = -(cos t, sin t), e_u = (-sin t, cos t)).
+struct alignas(16) ViewCtx2 {
+    float R0, R1, dc0, dc1;
+    float k;     // flat: sdd / pitch; parallel: the shadow's half-width + margin
+    int u0, u1;  // bins of the work item
+    int rbase;   // table position of bin 0 of the item
+};
+
+// Per-view data of a 3D backprojection CTA.
+struct ViewCtx3 {
     float S[3], dc[3], eu[3], ev[3];
     float sdd;
-    float hw_u, hw_v;
     int u0, u1, v0, v1;
-    int64_t ray_off;
+    int rbase;   // table position of bin (0, v0) of the item
 };
-constexpr int kViewBatch = 96;
-// bins added on each side of a voxel's shadow window: covers the series atan
-// (below 0.011 bin at the finest pitch used) and FP32 rounding
-constexpr float kShadowMargin = 0.02f;
+
+template <int DIM>
+struct ViewCtxOf { using type = ViewCtx3; };
+template <>
+struct ViewCtxOf<2> { using type = ViewCtx2; };
+
+__device__ __forceinline__ void stage_view(const DevGeom& G, const DevTile& t, const WorkItem& it,
+                                           ViewCtx2* c) {
+    const DevView& V = G.views[it.view];
+    const bool par = G.kind == PARALLEL_2D;
+    c->R0 = (t.T[0] - 0.5f * (float)t.n[0] + 0.5f) - (par ? 0.f : V.S[0]);
+    c->R1 = (t.T[1] - 0.5f * (float)t.n[1] + 0.5f) - (par ? 0.f : V.S[1]);
+    c->dc0 = V.dc[0];
+    c->dc1 = V.dc[1];
+    c->k = par ? fmaf(0.5f * (fabsf(V.dc[0]) + fabsf(V.dc[1])), G.inv_pu, kShadowMargin)
+               : V.sdd * G.inv_pu;
+    c->u0 = it.u0;
+    c->u1 = it.u1;
+    c->rbase = (int)it.ray_off - it.u0;
+}
+
+__device__ __forceinline__ void stage_view(const DevGeom& G, const DevTile&, const WorkItem& it,
+                                           ViewCtx3* c) {
+    const DevView& V = G.views[it.view];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        c->S[k] = V.S[k];
+        c->dc[k] = V.dc[k];
+        c->eu[k] = V.eu[k];
+        c->ev[k] = V.ev[k];
+    }
+    c->sdd = V.sdd;
+    c->u0 = it.u0;
+    c->u1 = it.u1;
+    c->v0 = it.v0;
+    c->v1 = it.v1;
+    c->rbase = (int)it.ray_off - it.u0;
+}
+
+// Length of the unit voxel [lo, hi) on the line of a 2D table record.
+__device__ __forceinline__ float slab2(const float4 a, const float lo[3], const float hi[3]) {
+    const float ta0 = (lo[0] - a.x) * a.z, tb0 = (hi[0] - a.x) * a.z;
+    const float ta1 = (lo[1] - a.y) * a.w, tb1 = (hi[1] - a.y) * a.w;
+    const float tin = fmaxf(fminf(ta0, tb0), fminf(ta1, tb1));
+    const float tout = fminf(fmaxf(ta0, tb0), fmaxf(ta1, tb1));
+    return fmaxf(tout - tin, 0.f);
+}
+
+__device__ __forceinline__ float slab3(const float4 a, const float4 b, const float lo[3],
+                                       const float hi[3]) {
+    const float ta0 = (lo[0] - a.x) * a.z, tb0 = (hi[0] - a.x) * a.z;
+    const float ta1 = (lo[1] - a.y) * a.w, tb1 = (hi[1] - a.y) * a.w;
+    const float ta2 = (lo[2] - b.y) * b.z, tb2 = (hi[2] - b.y) * b.z;
+    const float tin = fmaxf(fmaxf(fminf(ta0, tb0), fminf(ta1, tb1)), fminf(ta2, tb2));
+    const float tout = fminf(fminf(fmaxf(ta0, tb0), fmaxf(ta1, tb1)), fmaxf(ta2, tb2));
+    return fmaxf(tout - tin, 0.f);
+}
+
+__device__ __forceinline__ float4 rec_a(const RayRec* p) {
+    return *reinterpret_cast<const float4*>(p->a);
+}
+__device__ __forceinline__ float4 rec_b(const RayRec* p) {
+    return *reinterpret_cast<const float4*>(p->b);
+}
+
+// sum over the view's candidate bins of len * r for one voxel (2D)
+__device__ __forceinline__ float view_sum(const DevGeom& G, const ViewCtx2& c, float xf, float yf,
+                                          const float lo[3], const float hi[3],
+                                          const RayRec* __restrict__ tab) {
+    const float r0 = c.R0 + xf, r1 = c.R1 + yf;
+    const float depth = fmaf(r0, c.dc0, r1 * c.dc1);
+    const float lat = fmaf(r0, c.dc1, -(r1 * c.dc0));
+    const float wbase = fmaf(0.5f, (float)G.nu, -0.5f);  // bin k covers [k, k+1) + 1/2 shift
+    float wu, hu;
+    if (G.kind == PARALLEL_2D) {
+        wu = fmaf(lat, G.inv_pu, wbase);
+        hu = c.k;
+    } else {
+        // first-order shadow, widened for curvature (see voxel_shadow)
+        const float rd = rcp_approx(depth);
+        const float grow = fmaf(1.5f, rd, 1.0f);
+        const float l1 = fabsf(r0) + fabsf(r1);  // |d(r . e_u, r . d_c)|_1 terms of grad w
+        if (G.kind == FAN_2D_CURVED) {
+            float gam;
+            if (G.fast_arc) gam = atan_series(lat * rd);
+            else gam = atan2f(lat, depth);
+            wu = fmaf(gam, G.inv_pu, wbase);
+            hu = fmaf(0.5f * G.inv_pu * l1 * rcp_approx(fmaf(r0, r0, r1 * r1)), grow, kShadowMargin);
+        } else {
+            wu = fmaf(lat * rd, c.k, wbase);
+            hu = fmaf(0.5f * c.k * l1 * rd * rd, grow, kShadowMargin);
+        }
+    }
+    const int ku0 = max(c.u0, __float2int_ru(wu - hu));
+    const int ku1 = min(c.u1 - 1, __float2int_rd(wu + hu));
+    const RayRec* row = tab + c.rbase;
+    float s = 0.f;
+    int ku = ku0;
+    // two candidates per pass (most voxels have one or two): both loads in flight
+    for (; ku < ku1; ku += 2) {
+        const float4 a0 = rec_a(row + ku), a1 = rec_a(row + ku + 1);
+        const float q0 = row[ku].b[0], q1 = row[ku + 1].b[0];
+        s = fmaf(slab2(a0, lo, hi), q0, s);
+        s = fmaf(slab2(a1, lo, hi), q1, s);
+    }
+    if (ku == ku1) s = fmaf(slab2(rec_a(row + ku), lo, hi), row[ku].b[0], s);
+    return s;
+}
+
+// sum over the view's candidate bins of len * r for one voxel (3D)
+__device__ __forceinline__ float view_sum(const DevGeom& G, const ViewCtx3& c, const float P[3],
+                                          const float lo[3], const float hi[3],
+                                          const RayRec* __restrict__ tab) {
+    DevView V;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        V.S[k] = c.S[k];
+        V.dc[k] = c.dc[k];
+        V.eu[k] = c.eu[k];
+        V.ev[k] = c.ev[k];
+    }
+    V.sdd = c.sdd;
+    float wu, wv, hu, hv;
+    voxel_shadow<3>(G, V, P, &wu, &wv, &hu, &hv);
+    hu += kShadowMargin;
+    hv += kShadowMargin;
+    const int ku0 = max(c.u0, __float2int_ru(wu - 0.5f - hu));
+    const int ku1 = min(c.u1 - 1, __float2int_rd(wu - 0.5f + hu));
+    const int kv0 = max(c.v0, __float2int_ru(wv - 0.5f - hv));
+    const int kv1 = min(c.v1 - 1, __float2int_rd(wv - 0.5f + hv));
+    const int wdt = c.u1 - c.u0;
+    float s = 0.f;
+    for (int kv = kv0; kv <= kv1; ++kv) {
+        const RayRec* row = tab + c.rbase + (kv - c.v0) * wdt;
+        for (int ku = ku0; ku <= ku1; ++ku) {
+            const RayRec* rp = row + ku;
+            const float4 b = rec_b(rp);
+            s = fmaf(slab3(rec_a(rp), b, lo, hi), b.x, s);
+        }
+    }
+    return s;
+}
 
 template <int DIM>
 __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem* items,
                                                  const StepDesc& sd, int slot) {
+    using Ctx = typename ViewCtxOf<DIM>::type;
     __shared__ float part[kBPThreads];
     __shared__ double sh[kBPThreads / 32];
-    __shared__ ViewCtx vs[kViewBatch];
+    __shared__ Ctx vs[kViewBatch];
     cg::cluster_group cluster = cg::this_cluster();
     const DevGeom& G = a.G;
     const int C = (int)cluster.num_blocks();
@@ -321,13 +496,16 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
     const int rest = valid ? v / t.n[0] : 0;
     const int x1 = rest % t.n[1];
     const int x2 = rest / t.n[1];
-    // voxel box in tile-centred coordinates
-    float lo[3], P[3];
+    // voxel box [lo, hi) in tile-centred coordinates, centre P
+    float lo[3], hi[3], P[3];
     lo[0] = -0.5f * (float)t.n[0] + (float)x0;
     lo[1] = -0.5f * (float)t.n[1] + (float)x1;
     lo[2] = DIM == 3 ? -0.5f * (float)t.n[2] + (float)x2 : -0.5f;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) P[c] = c < DIM ? t.T[c] + lo[c] + 0.5f : 0.f;
+    for (int c = 0; c < 3; ++c) {
+        hi[c] = lo[c] + 1.0f;
+        P[c] = c < DIM ? t.T[c] + lo[c] + 0.5f : 0.f;
+    }
     const RayRec* __restrict__ tab = a.table + (int64_t)slot * a.table_stride;
     // views of this chunk: items w0 + chunk, w0 + chunk + C, ...
     const int n_mine = sd.w1 - sd.w0 > chunk ? (sd.w1 - sd.w0 - chunk + C - 1) / C : 0;
@@ -335,91 +513,13 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
     for (int base = 0; base < n_mine; base += kViewBatch) {
         const int nb = min(kViewBatch, n_mine - base);
         __syncthreads();
-        if ((int)threadIdx.x < nb) {
-            const WorkItem it = items[sd.w0 + chunk + (base + threadIdx.x) * C];
-            const DevView& V = G.views[it.view];
-            const DevVT& E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
-            ViewCtx& c = vs[threadIdx.x];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                c.S[k] = V.S[k];
-                c.dc[k] = V.dc[k];
-                c.eu[k] = V.eu[k];
-                c.ev[k] = V.ev[k];
-            }
-            c.sdd = V.sdd;
-            c.hw_u = E.hw_u;
-            c.hw_v = E.hw_v;
-            c.u0 = it.u0;
-            c.u1 = it.u1;
-            c.v0 = it.v0;
-            c.v1 = it.v1;
-            c.ray_off = it.ray_off;
-        }
+        if ((int)threadIdx.x < nb)
+            stage_view(G, t, items[sd.w0 + chunk + (base + threadIdx.x) * C], &vs[threadIdx.x]);
         __syncthreads();
         if (!valid) continue;
         for (int i = 0; i < nb; ++i) {
-            const ViewCtx& c = vs[i];
-            DevView V;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                V.S[k] = c.S[k];
-                V.dc[k] = c.dc[k];
-                V.eu[k] = c.eu[k];
-                V.ev[k] = c.ev[k];
-            }
-            V.sdd = c.sdd;
-            float wu, wv, hu, hv;
-            voxel_shadow(G, V, P, &wu, &wv, &hu, &hv);
-            hu += kShadowMargin;
-            int ku0 = max(c.u0, (int)ceilf(wu - 0.5f - hu));
-            int ku1 = min(c.u1 - 1, (int)floorf(wu - 0.5f + hu));
-            int kv0 = c.v0, kv1 = c.v1 - 1;
-            if (DIM == 3) {
-                hv += kShadowMargin;
-                kv0 = max(c.v0, (int)ceilf(wv - 0.5f - hv));
-                kv1 = min(c.v1 - 1, (int)floorf(wv - 0.5f + hv));
-            }
-            const int wdt = c.u1 - c.u0;
-            float view_sum = 0.f;  // a few terms; compensated across views below
-            for (int kv = kv0; kv <= kv1; ++kv) {
-                const int64_t rowoff = c.ray_off + (int64_t)(kv - c.v0) * wdt - c.u0;
-                for (int ku = ku0; ku <= ku1; ++ku) {
-                    const RayRec* rp = tab + rowoff + ku;
-                    const float4 ra = *reinterpret_cast<const float4*>(rp->a);
-                    float q[3], inv[3], r;
-                    q[0] = ra.x;
-                    q[1] = ra.y;
-                    inv[0] = ra.z;
-                    inv[1] = ra.w;
-                    if (DIM == 3) {
-                        const float4 rb = *reinterpret_cast<const float4*>(rp->b);
-                        r = rb.x;
-                        q[2] = rb.y;
-                        inv[2] = rb.z;
-                    } else {
-                        r = rp->b[0];
-                        q[2] = 0.f;
-                        inv[2] = INFINITY;
-                    }
-                    float tin = -INFINITY, tout = INFINITY;
-                    bool hit = true;
-#pragma unroll
-                    for (int k = 0; k < DIM; ++k) {
-                        if (isfinite(inv[k])) {
-                            float ta = (lo[k] - q[k]) * inv[k];
-                            float tb = (lo[k] + 1.0f - q[k]) * inv[k];
-                            tin = fmaxf(tin, fminf(ta, tb));
-                            tout = fminf(tout, fmaxf(ta, tb));
-                        } else {
-                            hit = hit && q[k] >= lo[k] && q[k] < lo[k] + 1.0f;
-                        }
-                    }
-                    float len = hit ? fmaxf(tout - tin, 0.f) : 0.f;
-                    view_sum = fmaf(len, r, view_sum);
-                }
-            }
-            acc.add(view_sum);
+            if constexpr (DIM == 2) acc.add(view_sum(G, vs[i], (float)x0, (float)x1, lo, hi, tab));
+            else acc.add(view_sum(G, vs[i], P, lo, hi, tab));
         }
     }
     part[threadIdx.x] = acc.s - acc.c;
