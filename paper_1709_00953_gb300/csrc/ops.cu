@@ -102,7 +102,14 @@ __device__ __forceinline__ void forward_single(const DevGeom& G, const WorkItem*
             float t0 = sub == 0 ? tin : fmaf((float)sub, dt, tin);
             float t1 = sub == L - 1 ? tout : fmaf((float)(sub + 1), dt, tin);
             Kahan acc;
-            walk<DIM>(q, inv, b, t0, t1, [&](int idx, float len) { acc.add(len * __ldg(x + idx)); });
+            float plen = 0.f, pxv = 0.f;  // gather consumed one crossing later
+            walk<DIM>(q, inv, b, t0, t1, [&](int idx, float len) {
+                const float xv = __ldg(x + idx);
+                acc.add(plen * pxv);
+                plen = len;
+                pxv = xv;
+            });
+            acc.add(plen * pxv);
             part = acc.s - acc.c;
         }
         ray = ray_index(G, it.view, ku, kv);
@@ -153,16 +160,25 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
             float dt = (tout - tin) * (1.0f / L);
             float t0 = sub == 0 ? tin : fmaf((float)sub, dt, tin);
             float t1 = sub == L - 1 ? tout : fmaf((float)(sub + 1), dt, tin);
+            // software-pipelined gather: the (x, g) pair of a crossing is
+            // consumed at the next crossing, so its load overlaps one step of
+            // the walk (same terms, same order)
             Kahan ax, ag;
+            float plen = 0.f;
+            float2 pe = make_float2(0.f, 0.f);
             nz = walk<DIM>(q, inv, b, t0, t1, [&](int idx, float len) {
                 const float2 e = __ldg(xg + idx);
-                ax.add(len * e.x);
-                ag.add(len * e.y);
+                ax.add(plen * pe.x);
+                ag.add(plen * pe.y);
+                plen = len;
+                pe = e;
                 if (len > 0.f) {
                     if (first_idx < 0) first_idx = idx;
                     last_idx = idx;
                 }
             });
+            ax.add(plen * pe.x);
+            ag.add(plen * pe.y);
             pp = ax.s - ax.c;
             qp = ag.s - ag.c;
         }
