@@ -289,8 +289,10 @@ int validate_params(const Partition& p, const csgd_solver_params* prm) {
 }
 
 int64_t bp_partials_per_slot(const csgd_partition* P) {
-    // one g^T g partial per backprojection CTA of a slot (one thread per voxel)
-    return std::max<int64_t>(1, (P->p.max_tile_voxels + 255) / 256);
+    // one g^T g partial per backprojection CTA of a slot (one voxel patch each)
+    int64_t n = 1;
+    for (const DevTile& t : P->p.tiles_h) n = std::max<int64_t>(n, bp_blocks(t, P->p.dg.dim));
+    return n;
 }
 
 int solver_reset_device(csgd_solver* S, cudaStream_t s) {

@@ -7,13 +7,11 @@
 //                  residual r of every ray of every slot, set up once.
 //   k_backproject  g_J = (A_I^J)^T r_I (Eq. 'direction'): voxel-driven gather over
 //                  the ray table (each voxel sums len * r over the bins of its
-//                  shadow), partial sums of the view chunks reduced across the
-//                  CTAs of a thread-block cluster through distributed shared
-//                  memory, g^T g in FP64.  No atomics.
+//                  shadow), the partial sums of a CTA's view groups added in
+//                  shared memory in a fixed order, g^T g in FP64.  No atomics.
 //   k_epilogue     z_I^j = p + mu q, r -= z_new - z_old (the refresh of Alg. 2-4
 //                  applied incrementally), x^_J += x_J + mu g_J.
 //   k_average      x_J = x^_J / count_J at the end of an epoch.
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdio.h>
 
@@ -23,14 +21,13 @@
 #include "device.cuh"
 #include "ops.h"
 
-namespace cg = cooperative_groups;
-
 namespace csgd {
 
 namespace {
 
 constexpr int kFwdThreads = 256;
-constexpr int kBPThreads = 256;
+constexpr int kBPMaxChunks = 8;
+constexpr int kBPMaxThreads = kBPVox * kBPMaxChunks;
 constexpr int kEpiThreads = 256;
 
 __device__ __forceinline__ Box tile_box(const DevTile& t, int dim, int base, int s1, int s2) {
@@ -322,9 +319,7 @@ struct BPArgs {
 // holds a ray parallel to an axis whose q lies exactly on a face of that axis
 // (see ray_table_item), so no crossing is 0 * inf and the clip needs no special
 // case: a parallel ray's crossings are +-inf, which constrain nothing when q is
-// inside the slab and empty the interval when it is outside.  No atomics: the C
-// CTAs of a cluster (one per view chunk) add their partial sums through
-// distributed shared memory in a fixed order.
+// inside the slab and empty the interval when it is outside.
 
 // bins added on each side of a voxel's shadow window: covers the series atan
 // (below 0.011 bin at the finest pitch used), the approximate reciprocals
@@ -415,10 +410,17 @@ __device__ __forceinline__ float4 rec_b(const RayRec* p) {
     return *reinterpret_cast<const float4*>(p->b);
 }
 
-// sum over the view's candidate bins of len * r for one voxel (2D)
-__device__ __forceinline__ float view_sum(const DevGeom& G, const ViewCtx2& c, float xf, float yf,
-                                          const float lo[3], const float hi[3],
-                                          const RayRec* __restrict__ tab) {
+// Candidate bins of one voxel in one view (2D), with the records of the first
+// two already requested.
+struct Cand2 {
+    float4 a0, a1;
+    float rA, rB;
+    int ku0, ku1;
+    const RayRec* row;
+};
+
+__device__ __forceinline__ Cand2 view_cands(const DevGeom& G, const ViewCtx2& c, float xf, float yf,
+                                            const RayRec* __restrict__ tab) {
     const float r0 = c.R0 + xf, r1 = c.R1 + yf;
     const float depth = fmaf(r0, c.dc0, r1 * c.dc1);
     const float lat = fmaf(r0, c.dc1, -(r1 * c.dc0));
@@ -443,19 +445,29 @@ __device__ __forceinline__ float view_sum(const DevGeom& G, const ViewCtx2& c, f
             hu = fmaf(0.5f * c.k * l1 * rd * rd, grow, kShadowMargin);
         }
     }
-    const int ku0 = max(c.u0, __float2int_ru(wu - hu));
-    const int ku1 = min(c.u1 - 1, __float2int_rd(wu + hu));
-    const RayRec* row = tab + c.rbase;
-    float s = 0.f;
-    int ku = ku0;
-    // two candidates per pass (most voxels have one or two): both loads in flight
-    for (; ku < ku1; ku += 2) {
-        const float4 a0 = rec_a(row + ku), a1 = rec_a(row + ku + 1);
-        const float q0 = row[ku].b[0], q1 = row[ku + 1].b[0];
-        s = fmaf(slab2(a0, lo, hi), q0, s);
-        s = fmaf(slab2(a1, lo, hi), q1, s);
-    }
-    if (ku == ku1) s = fmaf(slab2(rec_a(row + ku), lo, hi), row[ku].b[0], s);
+    Cand2 k;
+    k.ku0 = max(c.u0, __float2int_ru(wu - hu));
+    k.ku1 = min(c.u1 - 1, __float2int_rd(wu + hu));
+    k.row = tab + c.rbase;
+    // The first two candidates without branches (most voxels have one or two,
+    // and lanes of a warp differ): both records are loaded from bins clamped
+    // into the item and the residual of a bin outside the window is zeroed.
+    const int kA = min(k.ku0, c.u1 - 1);
+    const int kB = min(kA + 1, c.u1 - 1);
+    k.a0 = rec_a(k.row + kA);
+    k.a1 = rec_a(k.row + kB);
+    const float rA = k.row[kA].b[0], rB = k.row[kB].b[0];
+    k.rA = k.ku0 <= k.ku1 ? rA : 0.f;
+    k.rB = k.ku0 < k.ku1 ? rB : 0.f;
+    return k;
+}
+
+// sum over the candidate bins of len * r for one voxel (2D)
+__device__ __forceinline__ float cand_sum(const Cand2& k, const float lo[3], const float hi[3]) {
+    float s = fmaf(slab2(k.a0, lo, hi), k.rA, 0.f);
+    s = fmaf(slab2(k.a1, lo, hi), k.rB, s);
+    for (int ku = k.ku0 + 2; ku <= k.ku1; ++ku)
+        s = fmaf(slab2(rec_a(k.row + ku), lo, hi), k.row[ku].b[0], s);
     return s;
 }
 
@@ -493,25 +505,32 @@ __device__ __forceinline__ float view_sum(const DevGeom& G, const ViewCtx3& c, c
     return s;
 }
 
+// A backprojection CTA owns a patch of kBPVox voxels of the tile and splits the
+// views of its slot among C = blockDim.x / kBPVox thread groups (view i goes to group
+// i mod C); the C partial sums of a voxel are added in shared memory in group
+// order.  C is chosen per launch so that the grid fills whole waves.
 template <int DIM>
 __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem* items,
                                                  const StepDesc& sd, int slot) {
     using Ctx = typename ViewCtxOf<DIM>::type;
-    __shared__ float part[kBPThreads];
-    __shared__ double sh[kBPThreads / 32];
+    __shared__ float part[kBPMaxThreads];
+    __shared__ double sh[kBPMaxThreads / 32];
     __shared__ Ctx vs[kViewBatch];
-    cg::cluster_group cluster = cg::this_cluster();
     const DevGeom& G = a.G;
-    const int C = (int)cluster.num_blocks();
-    const int chunk = (int)cluster.block_rank();
+    const int C = (int)blockDim.x / kBPVox;
+    const int chunk = (int)threadIdx.x / kBPVox;
+    const int lv = (int)threadIdx.x % kBPVox;
     const DevTile t = G.tiles[sd.j];
-    const int nvox = t.n[0] * t.n[1] * t.n[2];
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = v < nvox;
-    const int x0 = valid ? v % t.n[0] : 0;
-    const int rest = valid ? v / t.n[0] : 0;
-    const int x1 = rest % t.n[1];
-    const int x2 = rest / t.n[1];
+    // the CTA's patch of the tile (patches tile it in x-fastest order) and this
+    // thread's voxel in it: a compact patch shares candidate rays among its voxels
+    constexpr int P0 = DIM == 2 ? 8 : 4, P1 = DIM == 2 ? 8 : 4;
+    const int nb0 = (t.n[0] + P0 - 1) / P0, nb1 = (t.n[1] + P1 - 1) / P1;
+    const int b0 = blockIdx.x % nb0, b12 = blockIdx.x / nb0;
+    const int x0 = b0 * P0 + lv % P0;
+    const int x1 = (b12 % nb1) * P1 + (lv / P0) % P1;
+    const int x2 = DIM == 3 ? (b12 / nb1) * 4 + lv / (P0 * P1) : 0;
+    const bool valid = x0 < t.n[0] && x1 < t.n[1] && x2 < t.n[2];
+    const int v = (x2 * t.n[1] + x1) * t.n[0] + x0;  // tile-local voxel index
     // voxel box [lo, hi) in tile-centred coordinates, centre P
     float lo[3], hi[3], P[3];
     lo[0] = -0.5f * (float)t.n[0] + (float)x0;
@@ -523,54 +542,60 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
         P[c] = c < DIM ? t.T[c] + lo[c] + 0.5f : 0.f;
     }
     const RayRec* __restrict__ tab = a.table + (int64_t)slot * a.table_stride;
-    // views of this chunk: items w0 + chunk, w0 + chunk + C, ...
-    const int n_mine = sd.w1 - sd.w0 > chunk ? (sd.w1 - sd.w0 - chunk + C - 1) / C : 0;
+    const int n_items = sd.w1 - sd.w0;
     Kahan acc;
-    for (int base = 0; base < n_mine; base += kViewBatch) {
-        const int nb = min(kViewBatch, n_mine - base);
+    for (int base = 0; base < n_items; base += kViewBatch) {
+        const int nb = min(kViewBatch, n_items - base);
         __syncthreads();
-        if ((int)threadIdx.x < nb)
-            stage_view(G, t, items[sd.w0 + chunk + (base + threadIdx.x) * C], &vs[threadIdx.x]);
+        for (int k = threadIdx.x; k < nb; k += blockDim.x)
+            stage_view(G, t, items[sd.w0 + base + k], &vs[k]);
         __syncthreads();
         if (!valid) continue;
-        for (int i = 0; i < nb; ++i) {
-            if constexpr (DIM == 2) acc.add(view_sum(G, vs[i], (float)x0, (float)x1, lo, hi, tab));
-            else acc.add(view_sum(G, vs[i], P, lo, hi, tab));
+        if constexpr (DIM == 2) {
+            // two views per pass: the second view's records are requested before
+            // the first view's lengths are computed
+            int i = chunk;
+            for (; i + C < nb; i += 2 * C) {
+                const Cand2 k0 = view_cands(G, vs[i], (float)x0, (float)x1, tab);
+                const Cand2 k1 = view_cands(G, vs[i + C], (float)x0, (float)x1, tab);
+                acc.add(cand_sum(k0, lo, hi));
+                acc.add(cand_sum(k1, lo, hi));
+            }
+            if (i < nb) acc.add(cand_sum(view_cands(G, vs[i], (float)x0, (float)x1, tab), lo, hi));
+        } else {
+            for (int i = chunk; i < nb; i += C) acc.add(view_sum(G, vs[i], P, lo, hi, tab));
         }
     }
     part[threadIdx.x] = acc.s - acc.c;
-    cluster.sync();
+    __syncthreads();
     double gg = 0.0;
-    if (chunk == 0) {
+    if (chunk == 0 && valid) {
         float s = 0.f;
-        for (int rr = 0; rr < C; ++rr) s += cluster.map_shared_rank(part, rr)[threadIdx.x];
+        for (int c = 0; c < C; ++c) s += part[c * kBPVox + lv];
         s *= G.h;
-        if (valid) {
-            if (a.mode == 0) {
-                reinterpret_cast<float2*>(a.gout)[(int64_t)slot * a.slot_stride + v] =
-                    make_float2(a.xt[t.voff + v], s);
-            } else {
-                int64_t gi = ((int64_t)(t.lo[2] + x2) * G.ny + (t.lo[1] + x1)) * G.nx + t.lo[0] + x0;
-                a.gout[gi] = a.accumulate ? a.gout[gi] + s : s;
-            }
-            gg = (double)s * (double)s;
+        if (a.mode == 0) {
+            reinterpret_cast<float2*>(a.gout)[(int64_t)slot * a.slot_stride + v] =
+                make_float2(a.xt[t.voff + v], s);
+        } else {
+            int64_t gi = ((int64_t)(t.lo[2] + x2) * G.ny + (t.lo[1] + x1)) * G.nx + t.lo[0] + x0;
+            a.gout[gi] = a.accumulate ? a.gout[gi] + s : s;
         }
+        gg = (double)s * (double)s;
     }
-    cluster.sync();
-    if (a.gg_part && chunk == 0) {
+    if (a.gg_part) {
         double bg = block_sum(gg, sh);
         if (threadIdx.x == 0) a.gg_part[(int64_t)slot * a.gg_stride + blockIdx.x] = bg;
     }
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kBPThreads) k_backproject_inline(
+__global__ void __maxnreg__(DIM == 2 ? 64 : 48) k_backproject_inline(
     const BPArgs a, const __grid_constant__ InlineItems it) {
     backproject_body<DIM>(a, it.items, it.step, 0);
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kBPThreads) k_backproject_solver(
+__global__ void __maxnreg__(DIM == 2 ? 64 : 48) k_backproject_solver(
     const BPArgs a, const WorkItem* __restrict__ items, const StepDesc* __restrict__ steps) {
     const StepDesc sd = steps[a.first + blockIdx.z];
     backproject_body<DIM>(a, items, sd, blockIdx.z);
@@ -691,41 +716,66 @@ __global__ void k_sq_residual(const float* y, const float* ax, int64_t n, double
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-BPPlan plan_backprojection(const DevGeom& G, const DevTile& tile, int nslots, int sm_count) {
-    // One thread per voxel; when a batch has fewer than ~2048 threads per SM the
-    // views of a slot are split into C chunks (one cluster of C CTAs per voxel
-    // block).
+// Resident backprojection CTAs per SM for C view groups (occupancy of the
+// compiled kernel), looked up once per device.
+static int bp_resident(int dim, int C) {
+    static std::mutex mu;
+    static int cache[kNoAllocMaxDevices][2][kBPMaxChunks + 1] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return 1;
+    std::lock_guard<std::mutex> lk(mu);
+    int& n = cache[dev][dim == 3][C];
+    if (n == 0) {
+        int r = 0;
+        cudaError_t e = dim == 2
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_backproject_solver<2>, kBPVox * C, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_backproject_solver<3>, kBPVox * C, 0);
+        n = (e == cudaSuccess && r > 0) ? r : 1;
+    }
+    return n;
+}
+
+BPPlan plan_backprojection(const DevGeom& G, const DevTile& tile, int nslots, int views,
+                           int sm_count) {
+    // Estimated time for C view groups: (waves of CTAs) x (views per thread +
+    // a fixed cost of staging, counted as 4 views) / (issue efficiency, taken
+    // as proportional to resident warps below 32 per SM).  Ties go to the
+    // smaller C.
     BPPlan p;
-    const int64_t nv = (int64_t)tile.n[0] * tile.n[1] * tile.n[2];
-    p.blocks = (int)((nv + kBPThreads - 1) / kBPThreads);
-    int64_t threads = (int64_t)p.blocks * kBPThreads * nslots;
-    int64_t want = (int64_t)2048 * sm_count;
-    int C = (int)((want + threads - 1) / threads);
-    p.C = std::max(1, std::min(8, C));
+    p.blocks = bp_blocks(tile, G.dim);
+    const int64_t grid = (int64_t)p.blocks * std::max(1, nslots);
+    views = std::max(1, views);
+    double best = 0.0;
+    p.C = 1;
+    for (int C = 1; C <= kBPMaxChunks; ++C) {
+        const int64_t per_sm = bp_resident(G.dim, C);
+        const int64_t cap = per_sm * sm_count;
+        const int64_t waves = (grid + cap - 1) / cap;
+        const double ctas_per_sm = std::min<double>((double)per_sm, (double)grid / sm_count);
+        const double eff = std::min(1.0, ctas_per_sm * (kBPVox / 32) * C / 32.0);
+        const double est = (double)waves * ((views + C - 1) / C + 4) / eff;
+        if (C == 1 || est < best) {
+            best = est;
+            p.C = C;
+        }
+        if (views <= C) break;
+    }
     return p;
 }
 
 static cudaError_t launch_bp_common(const DevGeom& G, const BPPlan& plan, int nslots,
                                     cudaStream_t s, const BPArgs& a, const InlineItems* inl,
                                     const WorkItem* items, const StepDesc* steps) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(plan.blocks, plan.C, nslots);
-    cfg.blockDim = dim3(kBPThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = plan.C;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    const dim3 grid((unsigned)plan.blocks, 1, (unsigned)nslots);
+    const dim3 block((unsigned)(kBPVox * plan.C));
     if (inl) {
-        if (G.dim == 2) return cudaLaunchKernelEx(&cfg, k_backproject_inline<2>, a, *inl);
-        return cudaLaunchKernelEx(&cfg, k_backproject_inline<3>, a, *inl);
+        if (G.dim == 2) k_backproject_inline<2><<<grid, block, 0, s>>>(a, *inl);
+        else k_backproject_inline<3><<<grid, block, 0, s>>>(a, *inl);
+    } else {
+        if (G.dim == 2) k_backproject_solver<2><<<grid, block, 0, s>>>(a, items, steps);
+        else k_backproject_solver<3><<<grid, block, 0, s>>>(a, items, steps);
     }
-    if (G.dim == 2) return cudaLaunchKernelEx(&cfg, k_backproject_solver<2>, a, items, steps);
-    return cudaLaunchKernelEx(&cfg, k_backproject_solver<3>, a, items, steps);
+    return cudaGetLastError();
 }
 
 // Rows of a per-item grid: enough CTAs per item to cover its rays with ~4
@@ -793,7 +843,7 @@ cudaError_t launch_backproject_inline(const DevGeom& G, const DevTile& tile,
                                                    (it.items[k].v1 - it.items[k].v0));
     cudaError_t e = launch_table(G, it.n, max_item, s, ta, &it, nullptr);
     if (e != cudaSuccess) return e;
-    BPPlan plan = plan_backprojection(G, tile, 1, sm_count);
+    BPPlan plan = plan_backprojection(G, tile, 1, it.n, sm_count);
     BPArgs a;
     a.G = G;
     a.first = 0;
@@ -849,7 +899,8 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
                          const StepDesc* steps, const BatchLaunch& b, const SolverBuffers& sb,
                          int sm_count, cudaStream_t s, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], s);
-    BPPlan plan = plan_backprojection(G, tile, b.nslots, sm_count);
+    BPPlan plan = plan_backprojection(G, tile, b.nslots, (b.n_items + b.nslots - 1) / b.nslots,
+                                      sm_count);
     // 1. g_J = (A_I^J)^T r_I per slot: ray table, then voxel-driven sums
     TableArgs ta;
     ta.G = G;

@@ -19,13 +19,22 @@ struct InlineItems {
     WorkItem items[kMaxInlineItems];
 };
 
-// Backprojection launch: one thread per voxel of the tile (`blocks` CTAs per
-// slot); the views of a slot are split among the C CTAs of a cluster.
+// Backprojection launch: `blocks` CTAs per slot, each owning a patch of kBPVox
+// voxels of the tile (8 x 8 in 2D, 4 x 4 x 4 in 3D) with its views split among
+// C thread groups of kBPVox threads.
+constexpr int kBPVox = 64;
+inline int bp_patch(int dim, int axis) { return dim == 2 ? (axis < 2 ? 8 : 1) : 4; }
+inline int bp_blocks(const DevTile& t, int dim) {
+    int b = 1;
+    for (int a = 0; a < 3; ++a) b *= (t.n[a] + bp_patch(dim, a) - 1) / bp_patch(dim, a);
+    return b;
+}
 struct BPPlan {
-    int blocks;  // CTAs per (slot, chunk)
-    int C;       // view chunks = CTAs per cluster
+    int blocks;  // CTAs per slot (one g^T g partial each)
+    int C;       // view groups per CTA
 };
-BPPlan plan_backprojection(const DevGeom& G, const DevTile& tile, int nslots, int sm_count);
+BPPlan plan_backprojection(const DevGeom& G, const DevTile& tile, int nslots, int views,
+                           int sm_count);
 
 // ---- stand-alone operators (inline items, one slot) -------------------------
 // out[ray] = (accumulate ? out[ray] : 0) + h * sum A x over the items' rays.
