@@ -194,6 +194,66 @@ __device__ __forceinline__ int walk(const float q[3], const float inv[3], const 
 }
 
 // Whole traversal of the box: clip, then walk.
+// The 2D walk producing its crossings in batches of B: f(idx, len) receives
+// arrays of B entries once per batch; entries past the end of the walk have
+// length 0 and index b.base.  Same crossings, same arithmetic and the same
+// order as walk<2>; a batch lets the caller have B independent loads in flight.
+template <int B, class F>
+__device__ __forceinline__ int walk2_batched(const float q[3], const float inv[3], const Box& b,
+                                             float tin, float tout, F&& f) {
+    int ix, iy;
+    float px, py, tx, ty;
+    int sx, sy;
+    {
+        const bool mx = isfinite(inv[0]), my = isfinite(inv[1]);
+        const float pa = mx ? q[0] + tin / inv[0] : q[0];
+        const float pb = my ? q[1] + tin / inv[1] : q[1];
+        ix = min(max((int)floorf(pa - b.lo[0]), 0), b.n[0] - 1);
+        iy = min(max((int)floorf(pb - b.lo[1]), 0), b.n[1] - 1);
+        const bool ux = mx && inv[0] > 0.f, uy = my && inv[1] > 0.f;
+        sx = ux ? 1 : -1;
+        sy = uy ? 1 : -1;
+        px = b.lo[0] + (float)(ix + (ux ? 1 : 0));
+        py = b.lo[1] + (float)(iy + (uy ? 1 : 0));
+        tx = mx ? (px - q[0]) * inv[0] : INFINITY;
+        ty = my ? (py - q[1]) * inv[1] : INFINITY;
+    }
+    int idx = b.base + ix * b.stride[0] + iy * b.stride[1];
+    const int dsx = sx * b.stride[0], dsy = sy * b.stride[1];
+    const float fsx = (float)sx, fsy = (float)sy;
+    const unsigned nx = (unsigned)b.n[0], ny = (unsigned)b.n[1];
+    float tc = tin;
+    int cnt = 0;
+    bool alive = true;
+    while (alive) {
+        int id[B];
+        float ln[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const bool bx = tx <= ty;
+            const float t = fminf(bx ? tx : ty, tout);
+            const float len = fmaxf(t - tc, 0.f);
+            ln[u] = alive ? len : 0.f;
+            id[u] = alive ? idx : b.base;
+            cnt += ln[u] > 0.f;
+            alive = alive && t < tout;
+            tc = t;
+            ix += bx ? sx : 0;
+            iy += bx ? 0 : sy;
+            idx += bx ? dsx : dsy;
+            px += bx ? fsx : 0.f;
+            py += bx ? 0.f : fsy;
+            const float nxt = (px - q[0]) * inv[0];
+            const float nyt = (py - q[1]) * inv[1];
+            tx = bx ? nxt : tx;
+            ty = bx ? ty : nyt;
+            alive = alive && (unsigned)ix < nx && (unsigned)iy < ny;
+        }
+        f(id, ln);
+    }
+    return cnt;
+}
+
 template <int DIM, class F>
 __device__ __forceinline__ int traverse(const float q[3], const float inv[3], const Box& b, F&& f) {
     float tin, tout;

@@ -26,6 +26,7 @@ namespace csgd {
 namespace {
 
 constexpr int kFwdThreads = 256;
+constexpr int kFwdBatch = 4;  // crossings per batch of gathers in the 2D dual forward
 constexpr int kBPMaxChunks = 8;
 constexpr int kBPMaxThreads = kBPVox * kBPMaxChunks;
 constexpr int kEpiThreads = 256;
@@ -125,10 +126,10 @@ __global__ void __launch_bounds__(kFwdThreads) k_project_inline(
 // p = A x_J and q = A g_J for every ray of a slot in one walk (z = p + mu q by
 // linearity), with ||q||^2 in FP64.  Rays come from the batch's ray table (set
 // up once for the backprojection), split over L lanes by parameter range.  Each
-// warp writes its partial sums; the last warp of the slot to finish adds them
-// in a fixed order and computes mu = beta g^T g / q^T q (no grid barrier).
+// CTA writes its partial sums; the last CTA of the slot to finish adds them in a
+// fixed order and computes mu = beta g^T g / q^T q (no grid barrier).
 template <int DIM, int L>
-__global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArgs a) {
+__global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     const DevGeom& G = a.G;
     const int slot = blockIdx.y;
     const StepDesc sd = a.steps[a.first + slot];
@@ -157,25 +158,64 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
             float dt = (tout - tin) * (1.0f / L);
             float t0 = sub == 0 ? tin : fmaf((float)sub, dt, tin);
             float t1 = sub == L - 1 ? tout : fmaf((float)(sub + 1), dt, tin);
-            // software-pipelined gather: the (x, g) pair of a crossing is
-            // consumed at the next crossing, so its load overlaps one step of
-            // the walk (same terms, same order)
             Kahan ax, ag;
-            float plen = 0.f;
-            float2 pe = make_float2(0.f, 0.f);
-            nz = walk<DIM>(q, inv, b, t0, t1, [&](int idx, float len) {
-                const float2 e = __ldg(xg + idx);
+            if constexpr (DIM == 2) {
+                // crossings in batches of kFwdBatch: the batch's (x, g) gathers are
+                // all in flight before any is used.  A batch's terms are added as a
+                // pairwise tree and the batch sum once into the lane's running sum:
+                // for n terms the rounding error is at most (n / 4 + 3) u sum |term|
+                // (u = 2^-24), below 1e-5 sum |term| while n < 650 (a lane meets at
+                // most n_x + n_y voxels: any tile up to 320 voxels a side).
+                float sx = 0.f, sy = 0.f;
+                nz = walk2_batched<kFwdBatch>(q, inv, b, t0, t1,
+                                              [&](const int (&id)[kFwdBatch], const float (&ln)[kFwdBatch]) {
+                    float2 e[kFwdBatch];
+#pragma unroll
+                    for (int u = 0; u < kFwdBatch; ++u)
+                        e[u] = ln[u] > 0.f ? __ldg(xg + id[u]) : make_float2(0.f, 0.f);
+                    float px[kFwdBatch], py[kFwdBatch];
+#pragma unroll
+                    for (int u = 0; u < kFwdBatch; ++u) {
+                        px[u] = ln[u] * e[u].x;
+                        py[u] = ln[u] * e[u].y;
+                        if (ln[u] > 0.f) {
+                            if (first_idx < 0) first_idx = id[u];
+                            last_idx = id[u];
+                        }
+                    }
+#pragma unroll
+                    for (int w = 1; w < kFwdBatch; w *= 2) {
+#pragma unroll
+                        for (int u = 0; u + w < kFwdBatch; u += 2 * w) {
+                            px[u] += px[u + w];
+                            py[u] += py[u + w];
+                        }
+                    }
+                    sx += px[0];
+                    sy += py[0];
+                });
+                ax.s = sx;
+                ag.s = sy;
+            } else {
+                // software-pipelined gather: the (x, g) pair of a crossing is
+                // consumed at the next crossing, so its load overlaps one step of
+                // the walk (same terms, same order)
+                float plen = 0.f;
+                float2 pe = make_float2(0.f, 0.f);
+                nz = walk<DIM>(q, inv, b, t0, t1, [&](int idx, float len) {
+                    const float2 e = __ldg(xg + idx);
+                    ax.add(plen * pe.x);
+                    ag.add(plen * pe.y);
+                    plen = len;
+                    pe = e;
+                    if (len > 0.f) {
+                        if (first_idx < 0) first_idx = idx;
+                        last_idx = idx;
+                    }
+                });
                 ax.add(plen * pe.x);
                 ag.add(plen * pe.y);
-                plen = len;
-                pe = e;
-                if (len > 0.f) {
-                    if (first_idx < 0) first_idx = idx;
-                    last_idx = idx;
-                }
-            });
-            ax.add(plen * pe.x);
-            ag.add(plen * pe.y);
+            }
             pp = ax.s - ax.c;
             qp = ag.s - ag.c;
         }
@@ -193,37 +233,48 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward_dual(const FwdSolverArg
         a.sb.q[ray] = qv;
         qq = (double)qv * (double)qv;
     }
-    // per-warp partials, then the last warp of the slot finishes
+    // per-CTA partials (warps added in order in shared memory), then the last
+    // CTA of the slot to finish adds the partials in a fixed order
+    __shared__ double s_q[kFwdThreads / 32];
+    __shared__ long long s_n[kFwdThreads / 32];
+    __shared__ unsigned s_last;
     const double wq = warp_sum(qq);
     const long long wn = warp_sum_ll(nz);
-    const int nwarps_block = blockDim.x >> 5;
-    const int wglob = blockIdx.x * nwarps_block + (threadIdx.x >> 5);
-    const int total = gridDim.x * nwarps_block;
-    unsigned last = 0;
     if (lane == 0) {
-        a.sb.qq_part[(int64_t)slot * a.sb.qq_stride + wglob] = wq;
-        if (wn) {
-            atomicAdd(a.sb.nnz, (unsigned long long)wn);
-            atomicAdd(a.sb.nnz_slot + slot, (unsigned long long)wn);
-        }
-        __threadfence();
-        unsigned prev = atomicAdd(a.sb.counters + slot, 1u);
-        last = prev == (unsigned)(total - 1);
+        s_q[threadIdx.x >> 5] = wq;
+        s_n[threadIdx.x >> 5] = wn;
     }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double cq = 0.0;
+        long long cn = 0;
+        for (int w = 0; w < kFwdThreads / 32; ++w) {
+            cq += s_q[w];
+            cn += s_n[w];
+        }
+        a.sb.qq_part[(int64_t)slot * a.sb.qq_stride + blockIdx.x] = cq;
+        if (cn) atomicAdd(a.sb.nnz_slot + slot, (unsigned long long)cn);
+        __threadfence();
+        const unsigned prev = atomicAdd(a.sb.counters + slot, 1u);
+        s_last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
     __threadfence();
-    // fixed-order sums (lane l takes partials l, l+32, ...; then a fixed butterfly)
+    // thread t adds partials t, t + blockDim.x, ... in order; then a fixed tree
     double qs = 0.0;
-    for (int w = lane; w < total; w += 32) qs += __ldcg(a.sb.qq_part + (int64_t)slot * a.sb.qq_stride + w);
-    qs = warp_sum(qs);
+    for (int w = threadIdx.x; w < (int)gridDim.x; w += blockDim.x)
+        qs += __ldcg(a.sb.qq_part + (int64_t)slot * a.sb.qq_stride + w);
+    qs = block_sum(qs, s_q);
     double gs = 0.0;
-    for (int w = lane; w < a.n_gg; w += 32) gs += __ldcg(a.sb.gg_part + (int64_t)slot * a.sb.gg_stride + w);
-    gs = warp_sum(gs);
-    if (lane == 0) {
+    for (int w = threadIdx.x; w < a.n_gg; w += blockDim.x)
+        gs += __ldcg(a.sb.gg_part + (int64_t)slot * a.sb.gg_stride + w);
+    gs = block_sum(gs, s_q);
+    if (threadIdx.x == 0) {
         double mu = qs > 0.0 ? sd.beta * gs / qs : 0.0;
         a.sb.mu[slot] = mu;
         unsigned long long nzs = atomicExch(a.sb.nnz_slot + slot, 0ull);
+        atomicAdd(a.sb.nnz, nzs);
         if (sd.step >= 0 && sd.step < a.sb.hist_cap) {
             double* hrow = a.sb.hist + kHistCols * sd.step;
             hrow[0] = sd.beta;
@@ -939,7 +990,7 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     const int L = lanes_per_ray(b.max_rays * b.nslots, sm_count);
     int64_t nb = (b.max_rays * L + kFwdThreads - 1) / kFwdThreads;
     if (nb < 1) nb = 1;
-    if (nb > sb.max_fwd_blocks || nb * (kFwdThreads / 32) > sb.qq_stride) return cudaErrorInvalidValue;
+    if (nb > sb.max_fwd_blocks || nb > sb.qq_stride) return cudaErrorInvalidValue;
     dim3 grid((unsigned)nb, b.nslots);
     if (G.dim == 2) {
         if (L == 1) k_forward_dual<2, 1><<<grid, kFwdThreads, 0, s>>>(f);
