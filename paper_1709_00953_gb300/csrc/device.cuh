@@ -261,6 +261,18 @@ __device__ __forceinline__ int traverse(const float q[3], const float inv[3], co
     return walk<DIM>(q, inv, b, tin, tout, f);
 }
 
+// Programmatic dependent launch.  pdl_trigger lets the next kernel of the
+// stream (launched with programmatic stream serialization) be scheduled while
+// this one runs; pdl_wait blocks until the previous kernel of the stream has
+// completed and its memory is visible.  A kernel calls pdl_wait before it reads
+// anything an earlier kernel writes and before its first global write, so the
+// chain of waits orders every kernel after all earlier ones.  Both are no-ops
+// in a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Reciprocal by the hardware approximation (rcp.approx: relative error about
 // 1e-7); used only where a result picks candidate bins under a margin.
 __device__ __forceinline__ float rcp_approx(float x) {

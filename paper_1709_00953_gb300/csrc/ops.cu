@@ -16,6 +16,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <utility>
 #include <mutex>
 
 #include "device.cuh"
@@ -130,10 +131,12 @@ __global__ void __launch_bounds__(kFwdThreads) k_project_inline(
 // fixed order and computes mu = beta g^T g / q^T q (no grid barrier).
 template <int DIM, int L>
 __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
+    pdl_trigger();
     const DevGeom& G = a.G;
     const int slot = blockIdx.y;
     const StepDesc sd = a.steps[a.first + slot];
     const DevTile t = G.tiles[sd.j];
+    pdl_wait();
     // (x_J, g_J) interleaved per voxel by the backprojection: one 8-byte gather per voxel
     const float2* __restrict__ xg = reinterpret_cast<const float2*>(a.sb.g) + (int64_t)slot * a.sb.g_stride;
     const int lane = threadIdx.x & 31;
@@ -310,6 +313,7 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
     const int wu = it.u1 - it.u0;
     const int nr = wu * (it.v1 - it.v0);
     RayRec* dst = a.table + (int64_t)it.slot * a.slot_stride + it.ray_off;
+    pdl_wait();  // r and the table buffer belong to earlier kernels until here
     for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < nr; k += gridDim.y * blockDim.x) {
         const int ku = it.u0 + k % wu;
         const int kv = it.v0 + k / wu;
@@ -343,6 +347,7 @@ __global__ void __launch_bounds__(256) k_ray_table_inline(const TableArgs a,
 template <int DIM>
 __global__ void __launch_bounds__(256) k_ray_table_solver(const TableArgs a,
                                                           const WorkItem* __restrict__ items) {
+    pdl_trigger();
     const WorkItem it = items[a.w_begin + blockIdx.x];
     ray_table_item<DIM>(a, it);
 }
@@ -601,6 +606,7 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
         for (int k = threadIdx.x; k < nb; k += blockDim.x)
             stage_view(G, t, items[sd.w0 + base + k], &vs[k]);
         __syncthreads();
+        if (base == 0) pdl_wait();  // the ray table is the previous kernel's
         if (!valid) continue;
         if constexpr (DIM == 2) {
             // two views per pass: the second view's records are requested before
@@ -617,6 +623,7 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
             for (int i = chunk; i < nb; i += C) acc.add(view_sum(G, vs[i], P, lo, hi, tab));
         }
     }
+    if (n_items <= 0) pdl_wait();
     part[threadIdx.x] = acc.s - acc.c;
     __syncthreads();
     double gg = 0.0;
@@ -648,6 +655,7 @@ __global__ void __maxnreg__(DIM == 2 ? 64 : 48) k_backproject_inline(
 template <int DIM>
 __global__ void __maxnreg__(DIM == 2 ? 64 : 48) k_backproject_solver(
     const BPArgs a, const WorkItem* __restrict__ items, const StepDesc* __restrict__ steps) {
+    pdl_trigger();
     const StepDesc sd = steps[a.first + blockIdx.z];
     backproject_body<DIM>(a, items, sd, blockIdx.z);
 }
@@ -671,6 +679,8 @@ struct EpiArgs {
 // CTAs 0 .. n_items-1 (x) update z and r on one work item's rays each; the
 // remaining CTAs add the batch's candidates into x^ of the tile.
 __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
+    pdl_trigger();
+    pdl_wait();
     const DevGeom& G = a.G;
     if ((int)blockIdx.x < a.n_items) {
         const WorkItem it = a.items[a.w_begin + blockIdx.x];
@@ -712,6 +722,8 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
 }
 
 __global__ void k_average(const DevGeom G, float* x, float* xh, const int32_t* cnt) {
+    pdl_trigger();
+    pdl_wait();
     const int j = blockIdx.y;
     const DevTile t = G.tiles[j];
     const int64_t nv = (int64_t)t.n[0] * t.n[1] * t.n[2];
@@ -724,6 +736,8 @@ __global__ void k_average(const DevGeom G, float* x, float* xh, const int32_t* c
 }
 
 __global__ void k_apply_pending(float* r, float* d, int64_t n) {
+    pdl_trigger();
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float dv = d[i];
@@ -767,6 +781,25 @@ __global__ void k_sq_residual(const float* y, const float* ax, int64_t n, double
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// before the previous kernel of the stream has finished and waits for it with
+// pdl_wait (kernels of the solver's batch sequence).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Resident backprojection CTAs per SM for C view groups (occupancy of the
 // compiled kernel), looked up once per device.
 static int bp_resident(int dim, int C) {
@@ -823,8 +856,8 @@ static cudaError_t launch_bp_common(const DevGeom& G, const BPPlan& plan, int ns
         if (G.dim == 2) k_backproject_inline<2><<<grid, block, 0, s>>>(a, *inl);
         else k_backproject_inline<3><<<grid, block, 0, s>>>(a, *inl);
     } else {
-        if (G.dim == 2) k_backproject_solver<2><<<grid, block, 0, s>>>(a, items, steps);
-        else k_backproject_solver<3><<<grid, block, 0, s>>>(a, items, steps);
+        if (G.dim == 2) return launch_pdl(k_backproject_solver<2>, grid, block, s, a, items, steps);
+        return launch_pdl(k_backproject_solver<3>, grid, block, s, a, items, steps);
     }
     return cudaGetLastError();
 }
@@ -845,8 +878,8 @@ static cudaError_t launch_table(const DevGeom& G, int n_items, int64_t max_item_
         if (G.dim == 2) k_ray_table_inline<2><<<grid, 256, 0, s>>>(t, *inl);
         else k_ray_table_inline<3><<<grid, 256, 0, s>>>(t, *inl);
     } else {
-        if (G.dim == 2) k_ray_table_solver<2><<<grid, 256, 0, s>>>(t, items);
-        else k_ray_table_solver<3><<<grid, 256, 0, s>>>(t, items);
+        if (G.dim == 2) return launch_pdl(k_ray_table_solver<2>, grid, dim3(256), s, t, items);
+        return launch_pdl(k_ray_table_solver<3>, grid, dim3(256), s, t, items);
     }
     return cudaGetLastError();
 }
@@ -993,15 +1026,15 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     if (nb > sb.max_fwd_blocks || nb > sb.qq_stride) return cudaErrorInvalidValue;
     dim3 grid((unsigned)nb, b.nslots);
     if (G.dim == 2) {
-        if (L == 1) k_forward_dual<2, 1><<<grid, kFwdThreads, 0, s>>>(f);
-        else if (L == 2) k_forward_dual<2, 2><<<grid, kFwdThreads, 0, s>>>(f);
-        else k_forward_dual<2, 4><<<grid, kFwdThreads, 0, s>>>(f);
+        if (L == 1) e = launch_pdl(k_forward_dual<2, 1>, grid, dim3(kFwdThreads), s, f);
+        else if (L == 2) e = launch_pdl(k_forward_dual<2, 2>, grid, dim3(kFwdThreads), s, f);
+        else e = launch_pdl(k_forward_dual<2, 4>, grid, dim3(kFwdThreads), s, f);
     } else {
-        if (L == 1) k_forward_dual<3, 1><<<grid, kFwdThreads, 0, s>>>(f);
-        else if (L == 2) k_forward_dual<3, 2><<<grid, kFwdThreads, 0, s>>>(f);
-        else k_forward_dual<3, 4><<<grid, kFwdThreads, 0, s>>>(f);
+        if (L == 1) e = launch_pdl(k_forward_dual<3, 1>, grid, dim3(kFwdThreads), s, f);
+        else if (L == 2) e = launch_pdl(k_forward_dual<3, 2>, grid, dim3(kFwdThreads), s, f);
+        else e = launch_pdl(k_forward_dual<3, 4>, grid, dim3(kFwdThreads), s, f);
     }
-    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], s);
     // 3. z, r and x^ updates
@@ -1020,8 +1053,8 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     const int64_t tv = (int64_t)tile.n[0] * tile.n[1] * tile.n[2];
     const int64_t vox_blocks = std::max<int64_t>(1, (tv + (int64_t)kEpiThreads * rows - 1) /
                                                        ((int64_t)kEpiThreads * rows));
-    k_epilogue<<<dim3((unsigned)(b.n_items + vox_blocks), rows), kEpiThreads, 0, s>>>(ea);
-    e = cudaGetLastError();
+    e = launch_pdl(k_epilogue, dim3((unsigned)(b.n_items + vox_blocks), rows), dim3(kEpiThreads), s, ea);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (ev) cudaEventRecord(ev[3], s);
     return e;
 }
@@ -1030,12 +1063,14 @@ cudaError_t launch_epoch_close(const DevGeom& G, const SolverBuffers& sb, int64_
                                int64_t max_tile_voxels, int sync_epoch, cudaStream_t s) {
     if (sync_epoch) {
         int64_t nb = std::min<int64_t>((n_rays + 255) / 256, 4096);
-        k_apply_pending<<<(unsigned)std::max<int64_t>(nb, 1), 256, 0, s>>>(sb.r, sb.d, n_rays);
+        cudaError_t e = launch_pdl(k_apply_pending, dim3((unsigned)std::max<int64_t>(nb, 1)), dim3(256),
+                                   s, sb.r, sb.d, n_rays);
+        if (e != cudaSuccess) return e;
     }
     int64_t nb = std::min<int64_t>((max_tile_voxels + 255) / 256, 1024);
-    k_average<<<dim3((unsigned)std::max<int64_t>(nb, 1), G.n_tiles), 256, 0, s>>>(G, sb.x, sb.xh,
-                                                                                  sb.cnt);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_average, dim3((unsigned)std::max<int64_t>(nb, 1), G.n_tiles), dim3(256),
+                               s, G, sb.x, sb.xh, (const int32_t*)sb.cnt);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaMemsetAsync(sb.cnt, 0, sizeof(int32_t) * G.n_tiles, s);
 }
