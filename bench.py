@@ -46,8 +46,8 @@ DEFAULT_STEPS = {"fan2d_512": 250, "parallel2d_64": 250, "cone3d_256": 12, "batc
 # the fan2d_512 workload (profiles/fan2d_512_kernels_ncu.md), valid only for the
 # kernel sources they were taken from (hash of ops.cu, device.cuh, common.h).
 NCU_TRAFFIC = {
-    ("fan2d_512_720x768_8x16_importance", "4563d5448771ca71"): {
-        "backproject": 2145792 + 1024, "forward_dual": 2526720},
+    ("fan2d_512_720x768_8x16_importance", "8411e977c42edde4"): {
+        "backproject": 2105344, "forward_dual": 2535936},
 }
 KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/csrc/device.cuh",
                   "paper_1709_00953_gb300/csrc/common.h")
