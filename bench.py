@@ -33,21 +33,24 @@ import numpy as np  # noqa: E402
 from synth import configs as C  # noqa: E402
 from synth import data as D  # noqa: E402
 
-# Algorithmic FP32 operations per non-zero of A_{I_g}^J, per kernel:
-#   traversal: next plane crossing (subtract, multiply) + choose the nearest (1)  = 3
-#   backprojection: length (1) + length * r (1) + add into the tile (1)            = 3
-#   dual forward: length (1) + two multiply-adds (2 x 2)                          = 5
-ALG_FLOP = {"backproject": 6.0, "forward_dual": 8.0}
+# Roofline of the operators (issue-bound, not HBM-bound): ray-voxel updates per
+# non-zero of A_{I_g}^J for each timed kernel, and the instructions one update
+# costs in an incremental Siddon step (choose the axis, clip to the segment,
+# length, clamp, advance index and plane, next crossing (2), gather, multiply-
+# add): the ceiling is SMs x 128 FP32 lanes x SM clock / 10 updates per second.
+UPDATES_PER_NNZ = {"backproject": 1, "forward_dual": 2}
+INSTR_PER_UPDATE = 10
 FP32_LANES_PER_SM = 128
 # enough solves for a timed region of about 1.5 s (several clock samples)
 DEFAULT_STEPS = {"fan2d_512": 250, "parallel2d_64": 250, "cone3d_256": 12, "batch_fan64": 20}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of
 # the fan2d_512 workload (profiles/fan2d_512_kernels_ncu.md), valid only for the
-# kernel sources they were taken from (hash of ops.cu, device.cuh, common.h).
+# kernel sources they were taken from (hash of ops.cu, device.cuh, common.h);
+# "backproject" is the ray table plus the gather, the unit the bench times.
 NCU_TRAFFIC = {
     ("fan2d_512_720x768_8x16_importance", "8411e977c42edde4"): {
-        "backproject": 2105344, "forward_dual": 2535936},
+        "backproject": 2105344 + 390400, "forward_dual": 2535936},
 }
 KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/csrc/device.cuh",
                   "paper_1709_00953_gb300/csrc/common.h")
@@ -350,15 +353,25 @@ def run_gpu(args, cfg, world, rank, local):
     dom = max(("backproject", "forward_dual"), key=lambda k: kern.get(k, {"ms": 0})["ms"])
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = ck["sm_mhz"] if ck else measured_peaks().get("clocks_under_load", {}).get("sm_mhz_median", 1507.0)
-    peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-    flop = ALG_FLOP[dom] * nnz_per_solve * args.steps
-    achieved = flop / (kern[dom]["ms"] / 1e3) / 1e12
+    peak = sm_count * FP32_LANES_PER_SM * mhz * 1e6 / INSTR_PER_UPDATE / 1e9
+    dom_s = kern[dom]["ms"] / 1e3
+    nnz_total = nnz_per_solve * args.steps
+    achieved = UPDATES_PER_NNZ[dom] * nnz_total / dom_s / 1e9
     traffic = NCU_TRAFFIC.get((cfg["name"], kernel_hash()), {}).get(dom)
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops,
-            "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-            "peak_basis": "FP32 FMA: %d SMs x %d lanes x 2 x %.0f MHz (median SM clock of this run)"
-                          % (sm_count, FP32_LANES_PER_SM, mhz),
-            "flop_per_nnz": ALG_FLOP[dom]}
+    hbm = measured_peaks().get("hbm_gbs")
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+            "unit": "Gupdates/s", "frac": achieved / peak, "traffic": traffic,
+            "peak_basis": "issue ceiling: %d SMs x %d FP32 lanes x %.0f MHz (median SM clock of this "
+                          "run) / %d instructions per ray-voxel update"
+                          % (sm_count, FP32_LANES_PER_SM, mhz, INSTR_PER_UPDATE),
+            "kernel_launches": int(kern[dom]["launches"]),
+            "csr_equivalent_gbs": 8.0 * nnz_total / dom_s / 1e9,
+            "csr_equivalent_note": "avoided work: the bytes a stored-matrix SpMV (FP32 value + int32 "
+                                   "index per non-zero) would stream for the same non-zeros"}
+    if traffic is not None:
+        roof["dram_gbs"] = traffic * kern[dom]["launches"] / dom_s / 1e9
+        if hbm:
+            roof["dram_frac_of_measured_hbm"] = roof["dram_gbs"] / hbm
     # per batch: ray table + backprojection, dual forward, epilogue; per epoch close:
     # averaging (+ pending-residual apply under epoch sync)
     close_kernels = 2 if cfg["solver"].get("sync", 0) == 1 else 1
