@@ -198,6 +198,13 @@ __device__ __forceinline__ int walk(const float q[3], const float inv[3], const 
 // arrays of B entries once per batch; entries past the end of the walk have
 // length 0 and index b.base.  Same crossings, same arithmetic and the same
 // order as walk<2>; a batch lets the caller have B independent loads in flight.
+// No per-step bounds test: while the walk is alive its voxel is inside the box,
+// because a plane coordinate is an exact float (lo + integer) and the crossing
+// of the box's far face, (face - q) * inv, is bit-identical to the exit
+// parameter of clip, so the walk ends (t >= tout) before it could step past
+// it; a start index one voxel behind the line only gives a zero-length first
+// segment.  The caller still masks its loads with the box size, and the batch
+// count is capped at the number of faces the box has.
 template <int B, class F>
 __device__ __forceinline__ int walk2_batched(const float q[3], const float inv[3], const Box& b,
                                              float tin, float tout, F&& f) {
@@ -221,11 +228,11 @@ __device__ __forceinline__ int walk2_batched(const float q[3], const float inv[3
     int idx = b.base + ix * b.stride[0] + iy * b.stride[1];
     const int dsx = sx * b.stride[0], dsy = sy * b.stride[1];
     const float fsx = (float)sx, fsy = (float)sy;
-    const unsigned nx = (unsigned)b.n[0], ny = (unsigned)b.n[1];
+    const int max_batches = (b.n[0] + b.n[1] + 2) / B + 1;
     float tc = tin;
     int cnt = 0;
     bool alive = true;
-    while (alive) {
+    for (int it = 0; alive && it < max_batches; ++it) {
         int id[B];
         float ln[B];
 #pragma unroll
@@ -238,8 +245,6 @@ __device__ __forceinline__ int walk2_batched(const float q[3], const float inv[3
             cnt += ln[u] > 0.f;
             alive = alive && t < tout;
             tc = t;
-            ix += bx ? sx : 0;
-            iy += bx ? 0 : sy;
             idx += bx ? dsx : dsy;
             px += bx ? fsx : 0.f;
             py += bx ? 0.f : fsy;
@@ -247,7 +252,6 @@ __device__ __forceinline__ int walk2_batched(const float q[3], const float inv[3
             const float nyt = (py - q[1]) * inv[1];
             tx = bx ? nxt : tx;
             ty = bx ? ty : nyt;
-            alive = alive && (unsigned)ix < nx && (unsigned)iy < ny;
         }
         f(id, ln);
     }

@@ -136,6 +136,7 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     const int slot = blockIdx.y;
     const StepDesc sd = a.steps[a.first + slot];
     const DevTile t = G.tiles[sd.j];
+    const int nvox = t.n[0] * t.n[1] * t.n[2];
     pdl_wait();
     // (x_J, g_J) interleaved per voxel by the backprojection: one 8-byte gather per voxel
     const float2* __restrict__ xg = reinterpret_cast<const float2*>(a.sb.g) + (int64_t)slot * a.sb.g_stride;
@@ -175,7 +176,8 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
                     float2 e[kFwdBatch];
 #pragma unroll
                     for (int u = 0; u < kFwdBatch; ++u)
-                        e[u] = ln[u] > 0.f ? __ldg(xg + id[u]) : make_float2(0.f, 0.f);
+                        e[u] = ln[u] > 0.f && (unsigned)id[u] < (unsigned)nvox
+                                   ? __ldg(xg + id[u]) : make_float2(0.f, 0.f);
                     float px[kFwdBatch], py[kFwdBatch];
 #pragma unroll
                     for (int u = 0; u < kFwdBatch; ++u) {
@@ -313,7 +315,7 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
     const int wu = it.u1 - it.u0;
     const int nr = wu * (it.v1 - it.v0);
     RayRec* dst = a.table + (int64_t)it.slot * a.slot_stride + it.ray_off;
-    pdl_wait();  // r and the table buffer belong to earlier kernels until here
+    bool waited = false;
     for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < nr; k += gridDim.y * blockDim.x) {
         const int ku = it.u0 + k % wu;
         const int kv = it.v0 + k / wu;
@@ -332,10 +334,15 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
             }
         }
         const int64_t ray = ray_index(G, it.view, ku, kv);
+        if (!waited) {
+            pdl_wait();  // r and the table buffer belong to earlier kernels until here
+            waited = true;
+        }
         *reinterpret_cast<float4*>(dst[k].a) = make_float4(q[0], q[1], inv[0], inv[1]);
         *reinterpret_cast<float4*>(dst[k].b) =
             make_float4(__ldg(a.r + ray), q[2], inv[2], __int_as_float((int)ray));
     }
+    if (!waited) pdl_wait();  // every thread orders the kernel after the previous one
 }
 
 template <int DIM>
@@ -382,6 +389,7 @@ struct BPArgs {
 // (relative error ~1e-7) and FP32 rounding
 constexpr float kShadowMargin = 0.02f;
 constexpr int kViewBatch = 96;
+constexpr int kBPViewsPerPass = 2;  // 2D gather: views whose candidate loads are in flight together
 
 // Per-view data of a 2D backprojection CTA, staged in shared memory.  For voxel
 // (i0, i1) of the tile, r = P - S = (R0 + i0, R1 + i1); its depth along the
@@ -609,16 +617,18 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
         if (base == 0) pdl_wait();  // the ray table is the previous kernel's
         if (!valid) continue;
         if constexpr (DIM == 2) {
-            // two views per pass: the second view's records are requested before
-            // the first view's lengths are computed
+            // kBPViewsPerPass views per pass: the records of all of them are
+            // requested before any length is computed
+            constexpr int V = kBPViewsPerPass;
             int i = chunk;
-            for (; i + C < nb; i += 2 * C) {
-                const Cand2 k0 = view_cands(G, vs[i], (float)x0, (float)x1, tab);
-                const Cand2 k1 = view_cands(G, vs[i + C], (float)x0, (float)x1, tab);
-                acc.add(cand_sum(k0, lo, hi));
-                acc.add(cand_sum(k1, lo, hi));
+            for (; i + (V - 1) * C < nb; i += V * C) {
+                Cand2 k[V];
+#pragma unroll
+                for (int u = 0; u < V; ++u) k[u] = view_cands(G, vs[i + u * C], (float)x0, (float)x1, tab);
+#pragma unroll
+                for (int u = 0; u < V; ++u) acc.add(cand_sum(k[u], lo, hi));
             }
-            if (i < nb) acc.add(cand_sum(view_cands(G, vs[i], (float)x0, (float)x1, tab), lo, hi));
+            for (; i < nb; i += C) acc.add(cand_sum(view_cands(G, vs[i], (float)x0, (float)x1, tab), lo, hi));
         } else {
             for (int i = chunk; i < nb; i += C) acc.add(view_sum(G, vs[i], P, lo, hi, tab));
         }
@@ -680,16 +690,18 @@ struct EpiArgs {
 // remaining CTAs add the batch's candidates into x^ of the tile.
 __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
     pdl_trigger();
-    pdl_wait();
     const DevGeom& G = a.G;
     if ((int)blockIdx.x < a.n_items) {
+        // the item and its (view, tile) constants are fixed for the solve: read
+        // them before waiting for the dual forward
         const WorkItem it = a.items[a.w_begin + blockIdx.x];
-        const float mu = (float)a.sb.mu[it.slot];
         const DevVT& E = G.vt[(int64_t)it.view * G.n_tiles + a.j];
         const int ew = E.u1 - E.u0;
         const int64_t zbase = E.zoff - (int64_t)E.v0 * ew - E.u0;
         const int wu = it.u1 - it.u0;
         const int nr = wu * (it.v1 - it.v0);
+        pdl_wait();
+        const float mu = (float)a.sb.mu[it.slot];
         for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < nr; k += gridDim.y * blockDim.x) {
             const int ku = it.u0 + k % wu;
             const int kv = it.v0 + k / wu;
@@ -704,6 +716,7 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
     } else {
         const DevTile t = G.tiles[a.j];
         const int64_t nv = (int64_t)t.n[0] * t.n[1] * t.n[2];
+        pdl_wait();
         float* xh = a.sb.xh + t.voff;
         const float* x = a.sb.x + t.voff;
         const int64_t nthreads = (int64_t)(gridDim.x - a.n_items) * gridDim.y * blockDim.x;
