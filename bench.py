@@ -226,6 +226,25 @@ def run_reference(args, cfg, world, rank):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank timing (replicas: every rank solves its own copy of the workload)
+# ---------------------------------------------------------------------------
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The largest of the ranks' times (every rank gets it): the job's time."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args, cfg, world, rank, local):
@@ -295,12 +314,9 @@ def run_gpu(args, cfg, world, rank, local):
         ck = clocks.stop()
         prof = solver.profile_read(reset=True)
         solver.profile(False)
-        ms = sum(a.elapsed_time(b) for a, b in ev)
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
         if world > 1:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             torch.distributed.barrier()
-            ms = float(t.item())
         return ms, wall, ck, prof
 
     # the headline: graph launches, no per-kernel events in the stream
@@ -309,8 +325,7 @@ def run_gpu(args, cfg, world, rank, local):
     # launch, on the solver's stream: per-kernel durations for the roofline and
     # the shares
     ms_instr, _, _, prof = timed(True, one_solve_direct)
-    updates = 3.0 * nnz_per_solve * args.steps * world
-    value = updates / (ms / 1e3)
+    value = job_rate(3.0 * nnz_per_solve * args.steps, world, ms)
 
     # ---- end to end through the public API: pinned host y in, host x out ----
     e2e = None
@@ -333,12 +348,8 @@ def run_gpu(args, cfg, world, rank, local):
             graph_e2e.launch()
             e_ev[k][1].record(stream)
             torch.cuda.synchronize()
-        e_ms = sum(a.elapsed_time(b) for a, b in e_ev)
-        if world > 1:
-            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": updates / (e_ms / 1e3), "unit": "updates/s",
+        e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e_ev), world, dev)
+        e2e = {"value": job_rate(3.0 * nnz_per_solve * args.steps, world, e_ms), "unit": "updates/s",
                "h2d_bytes_per_step": int(4 * p.n_rays), "d2h_bytes_per_step": int(4 * p.n_voxels),
                "ms_per_step": e_ms / args.steps}
 
@@ -420,6 +431,9 @@ def run_gpu(args, cfg, world, rank, local):
 # batched workload: 64 uneven fan problems, one graph launch vs one by one
 # ---------------------------------------------------------------------------
 def run_batch(args, world, rank, local):
+    # a single-GPU workload: under torchrun rank 0 runs it and the others exit
+    if rank != 0:
+        return 0
     import torch
     torch.cuda.set_device(local if world > 1 else 0)
     import __graft_entry__ as GE
@@ -492,6 +506,9 @@ def run_batch(args, world, rank, local):
 # serving workload: Poisson arrivals of mixed fan / cone jobs, continuous batching
 # ---------------------------------------------------------------------------
 def run_serve(args, world, rank, local):
+    # a single-GPU workload: under torchrun rank 0 runs it and the others exit
+    if rank != 0:
+        return 0
     import torch
     torch.cuda.set_device(local if world > 1 else 0)
     import __graft_entry__ as GE
