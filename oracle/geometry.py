@@ -13,7 +13,8 @@ origin, the rotation sense and the bin centring open; the readings used here
   [-n_a h / 2, n_a h / 2); voxel indices are row-major with x fastest;
 * view v at angle theta: central direction d_c = (-cos t, -sin t[, 0]) (from
   the source towards the centre), detector axis e_u = (-sin t, cos t[, 0]) and,
-  in 3D, e_v = (0, 0, 1);
+  in 3D, e_v = (0, 0, 1); a cos or sin below 1e-12 is taken as exactly 0 (a
+  view at a multiple of 90 degrees is axis-aligned; see ``axis_exact``);
 * detector bin k (of n) has its centre at (k - (n-1)/2) * pitch along its axis;
 * parallel beam: ray k is the line through s_k e_u with direction d_c;
 * fan / cone with a flat detector: source S = sod * (cos t, sin t[, 0]), pixel
@@ -117,12 +118,13 @@ class Geometry:
             sdd = float(np.linalg.norm(C - S))
             return S.copy(), (C - S) / sdd, eu.copy(), ev.copy(), sdd
         t = float(self.angles[v])
-        dc = np.array([-np.cos(t), -np.sin(t), 0.0])
-        eu = np.array([-np.sin(t), np.cos(t), 0.0])
+        c, s = axis_exact(np.cos(t)), axis_exact(np.sin(t))
+        dc = np.array([-c, -s, 0.0])
+        eu = np.array([-s, c, 0.0])
         ev = np.array([0.0, 0.0, 1.0])
         if self.kind == "parallel2d":
             return None, dc, eu, ev, 0.0
-        S = self.sod * np.array([np.cos(t), np.sin(t), 0.0])
+        S = self.sod * np.array([c, s, 0.0])
         return S, dc, eu, ev, float(self.sdd)
 
     def bin_u(self, k):
@@ -198,6 +200,16 @@ class Geometry:
             return wu, np.full_like(wu, 0.5)
         wv = lam * (rel @ ev) / self.pv + 0.5 * self.nv
         return wu, wv
+
+
+def axis_exact(v: float) -> float:
+    """A cosine or sine of a view angle below 1e-12 in magnitude is exactly 0.
+
+    Reading: a view at a multiple of 90 degrees is axis-aligned (cos(pi/2)
+    evaluates to 6e-17); a 1e-16 tilt would move the point where such a line
+    crosses a voxel face anywhere along it, which no finite precision can place.
+    """
+    return 0.0 if abs(v) < 1e-12 else float(v)
 
 
 def uniform_angles(n_views: int, span_deg: float, start_deg: float = 0.0) -> np.ndarray:

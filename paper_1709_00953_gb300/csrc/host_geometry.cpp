@@ -134,7 +134,13 @@ int geometry_from_desc(const csgd_geometry_desc* d, Geometry* g, std::string* er
             return CSGD_ERR_INVALID_ARG;
         }
         Frame& f = g->frames[v];
+        // a view at a multiple of 90 degrees is axis-aligned: cos and sin below
+        // 1e-12 (cos(pi/2) evaluates to 6e-17) are exactly 0, so that rays along an
+        // axis have no spurious 1e-16 tilt whose face crossings no FP32 set-up
+        // could place
         double c = cos(t), s = sin(t);
+        if (std::fabs(c) < 1e-12) c = 0.0;
+        if (std::fabs(s) < 1e-12) s = 0.0;
         f.dc[0] = -c; f.dc[1] = -s; f.dc[2] = 0;
         f.eu[0] = -s; f.eu[1] = c; f.eu[2] = 0;
         f.ev[0] = 0; f.ev[1] = 0; f.ev[2] = 1;

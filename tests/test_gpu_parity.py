@@ -71,8 +71,22 @@ def _abs_back(op, rows_blocks, j, r_rows):
     return OSd.backproject_box(g.grid, o, d, lo, hi, np.abs(r_rows))
 
 
+def _parallel_faces():
+    """Parallel beam with an odd bin count and a view at exactly 0 degrees: its
+    rays are parallel to x and lie on voxel faces (integer offsets), the case the
+    ray table moves one ulp off the face."""
+    cfg = C.parallel2d_64()
+    cfg.update(name="parallel_faces_32_6x33",
+               geom=dict(kind="parallel2d", n=(32, 32), h=1.0,
+                         angles=np.deg2rad([0.0, 30.0, 60.0, 90.0, 120.0, 150.0]), nu=33,
+                         nv=1, pu=1.0, pv=1.0, sod=0.0, sdd=0.0),
+               part=dict(tiles=(2, 2), view_blocks=2, det_blocks=(1, 1)))
+    return cfg
+
+
 CASES = {
     "parallel64": C.parallel2d_64(),
+    "parallel_faces": _parallel_faces(),
     "fan_curved_ragged": C.small_fan2d(n=96, views=48, nu=144, tiles=(3, 3), vb=4, du=2),
     "fan_flat_ragged": C.small_fan2d(n=80, views=40, nu=120, tiles=(2, 3), vb=4, du=3,
                                      curved=False),
