@@ -27,7 +27,7 @@ namespace csgd {
 namespace {
 
 constexpr int kFwdThreads = 256;
-constexpr int kFwdBatch = 4;  // crossings per batch of gathers in the 2D dual forward
+constexpr int kFwdBatch = 4;  // crossings per batch of gathers in the dual forward
 constexpr int kBPMaxChunks = 8;
 constexpr int kBPMaxThreads = kBPVox * kBPMaxChunks;
 constexpr int kEpiThreads = 256;
@@ -162,67 +162,45 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
             float dt = (tout - tin) * (1.0f / L);
             float t0 = sub == 0 ? tin : fmaf((float)sub, dt, tin);
             float t1 = sub == L - 1 ? tout : fmaf((float)(sub + 1), dt, tin);
-            Kahan ax, ag;
-            if constexpr (DIM == 2) {
-                // crossings in batches of kFwdBatch: the batch's (x, g) gathers are
-                // all in flight before any is used.  A batch's terms are added as a
-                // pairwise tree and the batch sum once into the lane's running sum:
-                // for n terms the rounding error is at most (n / 4 + 3) u sum |term|
-                // (u = 2^-24), below 1e-5 sum |term| while n < 650 (a lane meets at
-                // most n_x + n_y voxels: any tile up to 320 voxels a side).
-                float sx = 0.f, sy = 0.f;
-                nz = walk2_batched<kFwdBatch>(q, inv, b, t0, t1,
-                                              [&](const int (&id)[kFwdBatch], const float (&ln)[kFwdBatch]) {
-                    float2 e[kFwdBatch];
+            // crossings in batches of kFwdBatch: the batch's (x, g) gathers are
+            // all in flight before any is used.  A batch's terms are added as a
+            // pairwise tree and the batch sum once into the lane's running sum:
+            // for n terms the rounding error is at most (n / 4 + 3) u sum |term|
+            // (u = 2^-24), below 1e-5 sum |term| while n < 650 (a lane meets at
+            // most n_x + n_y (+ n_z) voxels of its tile: any 2D tile up to 320
+            // voxels a side, any 3D tile up to 216).
+            float sx = 0.f, sy = 0.f;
+            auto batch = [&](const int (&id)[kFwdBatch], const float (&ln)[kFwdBatch]) {
+                float2 e[kFwdBatch];
 #pragma unroll
-                    for (int u = 0; u < kFwdBatch; ++u)
-                        e[u] = ln[u] > 0.f && (unsigned)id[u] < (unsigned)nvox
-                                   ? __ldg(xg + id[u]) : make_float2(0.f, 0.f);
-                    float px[kFwdBatch], py[kFwdBatch];
+                for (int u = 0; u < kFwdBatch; ++u)
+                    e[u] = ln[u] > 0.f && (unsigned)id[u] < (unsigned)nvox
+                               ? __ldg(xg + id[u]) : make_float2(0.f, 0.f);
+                float px[kFwdBatch], py[kFwdBatch];
 #pragma unroll
-                    for (int u = 0; u < kFwdBatch; ++u) {
-                        px[u] = ln[u] * e[u].x;
-                        py[u] = ln[u] * e[u].y;
-                        if (ln[u] > 0.f) {
-                            if (first_idx < 0) first_idx = id[u];
-                            last_idx = id[u];
-                        }
+                for (int u = 0; u < kFwdBatch; ++u) {
+                    px[u] = ln[u] * e[u].x;
+                    py[u] = ln[u] * e[u].y;
+                    if (ln[u] > 0.f) {
+                        if (first_idx < 0) first_idx = id[u];
+                        last_idx = id[u];
                     }
+                }
 #pragma unroll
-                    for (int w = 1; w < kFwdBatch; w *= 2) {
+                for (int w = 1; w < kFwdBatch; w *= 2) {
 #pragma unroll
-                        for (int u = 0; u + w < kFwdBatch; u += 2 * w) {
-                            px[u] += px[u + w];
-                            py[u] += py[u + w];
-                        }
+                    for (int u = 0; u + w < kFwdBatch; u += 2 * w) {
+                        px[u] += px[u + w];
+                        py[u] += py[u + w];
                     }
-                    sx += px[0];
-                    sy += py[0];
-                });
-                ax.s = sx;
-                ag.s = sy;
-            } else {
-                // software-pipelined gather: the (x, g) pair of a crossing is
-                // consumed at the next crossing, so its load overlaps one step of
-                // the walk (same terms, same order)
-                float plen = 0.f;
-                float2 pe = make_float2(0.f, 0.f);
-                nz = walk<DIM>(q, inv, b, t0, t1, [&](int idx, float len) {
-                    const float2 e = __ldg(xg + idx);
-                    ax.add(plen * pe.x);
-                    ag.add(plen * pe.y);
-                    plen = len;
-                    pe = e;
-                    if (len > 0.f) {
-                        if (first_idx < 0) first_idx = idx;
-                        last_idx = idx;
-                    }
-                });
-                ax.add(plen * pe.x);
-                ag.add(plen * pe.y);
-            }
-            pp = ax.s - ax.c;
-            qp = ag.s - ag.c;
+                }
+                sx += px[0];
+                sy += py[0];
+            };
+            if constexpr (DIM == 2) nz = walk2_batched<kFwdBatch>(q, inv, b, t0, t1, batch);
+            else nz = walk3_batched<kFwdBatch>(q, inv, b, t0, t1, batch);
+            pp = sx;
+            qp = sy;
         }
     }
     if (L > 1) {
@@ -557,10 +535,25 @@ __device__ __forceinline__ float view_sum(const DevGeom& G, const ViewCtx3& c, c
     const int kv0 = max(c.v0, __float2int_ru(wv - 0.5f - hv));
     const int kv1 = min(c.v1 - 1, __float2int_rd(wv - 0.5f + hv));
     const int wdt = c.u1 - c.u0;
-    float s = 0.f;
+    const RayRec* base = tab + c.rbase - c.v0 * wdt;  // + kv * wdt + ku
+    // the first 2 x 2 candidates without branches (bins clamped into the item,
+    // residuals outside the window zeroed), the rest in loops (rare)
+    const int kA = min(ku0, c.u1 - 1), kB = min(kA + 1, c.u1 - 1);
+    const int vA = min(kv0, c.v1 - 1), vB = min(vA + 1, c.v1 - 1);
+    const bool uA = ku0 <= ku1, uB = ku0 < ku1, wA = kv0 <= kv1, wB = kv0 < kv1;
+    const RayRec* p00 = base + vA * wdt + kA;
+    const RayRec* p01 = base + vA * wdt + kB;
+    const RayRec* p10 = base + vB * wdt + kA;
+    const RayRec* p11 = base + vB * wdt + kB;
+    const float4 a00 = rec_a(p00), b00 = rec_b(p00), a01 = rec_a(p01), b01 = rec_b(p01);
+    const float4 a10 = rec_a(p10), b10 = rec_b(p10), a11 = rec_a(p11), b11 = rec_b(p11);
+    float s = fmaf(slab3(a00, b00, lo, hi), uA && wA ? b00.x : 0.f, 0.f);
+    s = fmaf(slab3(a01, b01, lo, hi), uB && wA ? b01.x : 0.f, s);
+    s = fmaf(slab3(a10, b10, lo, hi), uA && wB ? b10.x : 0.f, s);
+    s = fmaf(slab3(a11, b11, lo, hi), uB && wB ? b11.x : 0.f, s);
     for (int kv = kv0; kv <= kv1; ++kv) {
-        const RayRec* row = tab + c.rbase + (kv - c.v0) * wdt;
-        for (int ku = ku0; ku <= ku1; ++ku) {
+        const RayRec* row = base + kv * wdt;
+        for (int ku = (kv < kv0 + 2 ? ku0 + 2 : ku0); ku <= ku1; ++ku) {
             const RayRec* rp = row + ku;
             const float4 b = rec_b(rp);
             s = fmaf(slab3(rec_a(rp), b, lo, hi), b.x, s);
@@ -657,13 +650,13 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
 }
 
 template <int DIM>
-__global__ void __maxnreg__(DIM == 2 ? 64 : 48) k_backproject_inline(
+__global__ void __maxnreg__(64) k_backproject_inline(
     const BPArgs a, const __grid_constant__ InlineItems it) {
     backproject_body<DIM>(a, it.items, it.step, 0);
 }
 
 template <int DIM>
-__global__ void __maxnreg__(DIM == 2 ? 64 : 48) k_backproject_solver(
+__global__ void __maxnreg__(64) k_backproject_solver(
     const BPArgs a, const WorkItem* __restrict__ items, const StepDesc* __restrict__ steps) {
     pdl_trigger();
     const StepDesc sd = steps[a.first + blockIdx.z];
