@@ -541,6 +541,9 @@ def run_serve(args, world, rank, local):
         "latency": {"p50_s": s["p50_latency_s"], "p99_s": s["p99_latency_s"],
                     "mean_s": s["mean_latency_s"]},
         "max_concurrency": srv.max_concurrency, "wall_s": wall,
+        "quality": "each job runs its fixed step count; served results equal solo solves bit "
+                   "for bit and match the FP64 oracle's solution of the same job within RMSE "
+                   "1e-3 (GPU tests)",
     }
     if ck:
         line["clocks"] = ck

@@ -727,17 +727,31 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
     }
 }
 
+// x_J = x^_J / count_J and x^_J = 0 for every tile (grid.y = tile), 16-byte
+// accesses over the aligned body of each tile's range.
 __global__ void k_average(const DevGeom G, float* x, float* xh, const int32_t* cnt) {
     pdl_trigger();
     pdl_wait();
     const int j = blockIdx.y;
     const DevTile t = G.tiles[j];
-    const int64_t nv = (int64_t)t.n[0] * t.n[1] * t.n[2];
+    const int64_t a0 = t.voff, a1 = t.voff + (int64_t)t.n[0] * t.n[1] * t.n[2];
+    const int64_t b0 = min(a1, (a0 + 3) & ~(int64_t)3), b1 = max(b0, a1 & ~(int64_t)3);
     const int c = cnt[j];
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        if (c > 0) x[t.voff + v] = xh[t.voff + v] / (float)c;
-        xh[t.voff + v] = 0.f;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    auto one = [&](int64_t v) {
+        if (c > 0) x[v] = xh[v] / (float)c;
+        xh[v] = 0.f;
+    };
+    if (tid < b0 - a0) one(a0 + tid);
+    if (tid < a1 - b1) one(b1 + tid);
+    float4* x4 = reinterpret_cast<float4*>(x + b0);
+    float4* h4 = reinterpret_cast<float4*>(xh + b0);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t k = tid; k < (b1 - b0) / 4; k += nth) {
+        const float4 h = h4[k];
+        if (c > 0) x4[k] = make_float4(h.x / (float)c, h.y / (float)c, h.z / (float)c, h.w / (float)c);
+        h4[k] = z4;
     }
 }
 
@@ -1073,7 +1087,7 @@ cudaError_t launch_epoch_close(const DevGeom& G, const SolverBuffers& sb, int64_
                                    s, sb.r, sb.d, n_rays);
         if (e != cudaSuccess) return e;
     }
-    int64_t nb = std::min<int64_t>((max_tile_voxels + 255) / 256, 1024);
+    int64_t nb = std::min<int64_t>((max_tile_voxels / 4 + 255) / 256, 1024);
     cudaError_t e = launch_pdl(k_average, dim3((unsigned)std::max<int64_t>(nb, 1), G.n_tiles), dim3(256),
                                s, G, sb.x, sb.xh, (const int32_t*)sb.cnt);
     if (e == cudaSuccess) e = cudaGetLastError();

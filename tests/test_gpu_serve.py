@@ -69,3 +69,23 @@ def test_budget_bounds_concurrency(mods):
     too_small = serve.Server(hbm_budget_bytes=biggest // 4, max_running=2)
     with pytest.raises(ValueError):
         too_small.run(_jobs(serve, 5))
+
+
+def test_served_results_match_the_oracle(mods):
+    """Served reconstructions against the FP64 oracle's solution of the same job
+    (same data, schedule and step count): RMSE <= 1e-3, the serving quality bar."""
+    from oracle.blocks import Partition as OPart
+    from oracle.geometry import Geometry as OGeom
+    from oracle.solver import OracleSolver
+    csgd, serve = mods
+    jobs = [j for j in _jobs(serve) if j.name.startswith(("serve_cone3d_03", "serve_fan2d_04"))]
+    assert len(jobs) == 2
+    srv = serve.Server(hbm_budget_bytes=8 << 30, max_running=8)
+    srv.run(jobs)
+    for j in jobs:
+        cfg = j.cfg
+        og = OGeom(**cfg["geom"])
+        op = OPart(og, cfg["part"]["tiles"], cfg["part"]["view_blocks"], cfg["part"]["det_blocks"])
+        xo = OracleSolver(op, cfg["solver"], j.y.astype(np.float64)).run(cfg["steps"])
+        rmse = float(np.sqrt(np.mean((j.x.astype(np.float64) - xo) ** 2)))
+        assert rmse <= 1e-3, (j.name, rmse)
