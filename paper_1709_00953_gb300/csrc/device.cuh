@@ -352,59 +352,6 @@ __device__ __forceinline__ float atan_series(float x) {
     return x * p;
 }
 
-// Bin coordinates (wu, wv) of a voxel centre P and the half-widths (hu, hv) of
-// the voxel's shadow, for choosing the candidate bins of a voxel: the shadow of
-// the unit voxel is [w - h1, w + h1] to first order, h1 = 0.5 sum_k |dw/dP_k|;
-// the second derivative of a perspective or angular map is at most ~2 |grad w|
-// / depth, so over half a voxel diagonal (|delta|^2 <= 3/4) the second-order
-// term is below 0.75 |grad w| / depth <= 1.5 h1 / depth: h = h1 (1 + 1.5 /
-// depth).  Callers add a small margin for rounding, the approximate
-// reciprocals and, when the curved detector spans |gamma| < 0.46 rad, the
-// series atan.
-template <int DIM>
-__device__ __forceinline__ void voxel_shadow(const DevGeom& G, const DevView& V, const float P[3],
-                                             float* wu, float* wv, float* hu, float* hv) {
-    if (DIM == 2 && G.kind == PARALLEL_2D) {
-        *wu = fmaf(P[0] * V.eu[0] + P[1] * V.eu[1], G.inv_pu, 0.5f * G.nu);
-        *hu = 0.5f * (fabsf(V.eu[0]) + fabsf(V.eu[1])) * G.inv_pu;
-        *wv = 0.5f;
-        *hv = 0.f;
-        return;
-    }
-    float r0 = P[0] - V.S[0], r1 = P[1] - V.S[1], r2 = P[2] - V.S[2];
-    float depth = r0 * V.dc[0] + r1 * V.dc[1] + r2 * V.dc[2];
-    float lu = r0 * V.eu[0] + r1 * V.eu[1] + r2 * V.eu[2];
-    float rd = rcp_approx(depth);
-    if (DIM == 2 && G.kind == FAN_2D_CURVED) {
-        float gam = G.fast_arc ? atan_series(lu * rd) : atan2f(lu, depth);
-        *wu = fmaf(gam, G.inv_pu, 0.5f * G.nu);
-        // d gamma / dP = (depth e_u - lu d_c) / (depth^2 + lu^2)
-        float sc = 0.5f * G.inv_pu * rcp_approx(fmaf(depth, depth, lu * lu));
-        *hu = sc * (fabsf(depth * V.eu[0] - lu * V.dc[0]) + fabsf(depth * V.eu[1] - lu * V.dc[1])) *
-              fmaf(1.5f, rd, 1.0f);
-        *wv = 0.5f;
-        *hv = 0.f;
-        return;
-    }
-    // flat detector: w = sdd * l / depth / pitch, dw/dP = sdd (depth e - l d_c) / depth^2 / pitch
-    float lam = V.sdd * rd;
-    *wu = fmaf(lam * lu, G.inv_pu, 0.5f * G.nu);
-    float sc = 0.5f * lam * rd * fmaf(1.5f, rd, 1.0f);
-    float hu_ = fabsf(depth * V.eu[0] - lu * V.dc[0]) + fabsf(depth * V.eu[1] - lu * V.dc[1]);
-    if (DIM == 3) {
-        float lv = r0 * V.ev[0] + r1 * V.ev[1] + r2 * V.ev[2];
-        *wv = fmaf(lam * lv, G.inv_pv, 0.5f * G.nv);
-        hu_ += fabsf(depth * V.eu[2] - lu * V.dc[2]);
-        float hv_ = fabsf(depth * V.ev[0] - lv * V.dc[0]) + fabsf(depth * V.ev[1] - lv * V.dc[1]) +
-                    fabsf(depth * V.ev[2] - lv * V.dc[2]);
-        *hv = sc * hv_ * G.inv_pv;
-    } else {
-        *wv = 0.5f;
-        *hv = 0.f;
-    }
-    *hu = sc * hu_ * G.inv_pu;
-}
-
 // Compensated (Kahan) accumulator for the FP32 ray sums.
 struct Kahan {
     float s = 0.f, c = 0.f;

@@ -284,6 +284,32 @@ struct TableArgs {
     int64_t slot_stride;
 };
 
+// Line of bin (ku, kv) of the item in tile-centred coordinates: q and 1/d.
+template <int DIM>
+__device__ __forceinline__ void table_ray(const DevGeom& G, const DevView& V, const DevVT& E,
+                                          const DevTile& tile, int ku, int kv, float q[3],
+                                          float inv[3]) {
+    float d[3];
+    ray_setup(G, V, E, ku, kv, q, d);
+    reciprocal(d, inv);
+    // A ray parallel to axis ax whose q_ax lies exactly on a voxel face moves
+    // one ulp up: it meets the same voxels (a face belongs to the voxel above
+    // it, for the walk as for the oracle) and (face - q_ax) / d_ax is never 0 / 0.
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+        if (isinf(inv[ax])) {
+            const float hn = 0.5f * (float)tile.n[ax];
+            const float face = (float)__float2int_rn(q[ax] + hn) - hn;
+            if (q[ax] == face) q[ax] = nextafterf(q[ax], INFINITY);
+        }
+    }
+}
+
+// The first kTablePre rays of a thread are set up before waiting for the
+// previous kernel (they need only the geometry); the residual is read and the
+// records written after it.
+constexpr int kTablePre = 4;
+
 template <int DIM>
 __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkItem& it) {
     const DevGeom& G = a.G;
@@ -293,34 +319,35 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
     const int wu = it.u1 - it.u0;
     const int nr = wu * (it.v1 - it.v0);
     RayRec* dst = a.table + (int64_t)it.slot * a.slot_stride + it.ray_off;
-    bool waited = false;
-    for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < nr; k += gridDim.y * blockDim.x) {
+    const int k0 = blockIdx.y * blockDim.x + threadIdx.x;
+    const int stride = gridDim.y * blockDim.x;
+    float pq[kTablePre][3], pi[kTablePre][3];
+#pragma unroll
+    for (int p = 0; p < kTablePre; ++p) {
+        const int k = k0 + p * stride;
+        if (k < nr) table_ray<DIM>(G, V, E, tile, it.u0 + k % wu, it.v0 + k / wu, pq[p], pi[p]);
+    }
+    pdl_wait();  // r and the table buffer belong to earlier kernels until here
+#pragma unroll
+    for (int p = 0; p < kTablePre; ++p) {
+        const int k = k0 + p * stride;
+        if (k < nr) {
+            const int64_t ray = ray_index(G, it.view, it.u0 + k % wu, it.v0 + k / wu);
+            *reinterpret_cast<float4*>(dst[k].a) = make_float4(pq[p][0], pq[p][1], pi[p][0], pi[p][1]);
+            *reinterpret_cast<float4*>(dst[k].b) =
+                make_float4(__ldg(a.r + ray), pq[p][2], pi[p][2], __int_as_float((int)ray));
+        }
+    }
+    for (int k = k0 + kTablePre * stride; k < nr; k += stride) {
         const int ku = it.u0 + k % wu;
         const int kv = it.v0 + k / wu;
-        float q[3], d[3], inv[3];
-        ray_setup(G, V, E, ku, kv, q, d);
-        reciprocal(d, inv);
-        // A ray parallel to axis ax whose q_ax lies exactly on a voxel face moves
-        // one ulp up: it meets the same voxels (a face belongs to the voxel above
-        // it, for the walk as for the oracle) and (face - q_ax) / d_ax is never 0 / 0.
-#pragma unroll
-        for (int ax = 0; ax < DIM; ++ax) {
-            if (isinf(inv[ax])) {
-                const float hn = 0.5f * (float)tile.n[ax];
-                const float face = (float)__float2int_rn(q[ax] + hn) - hn;
-                if (q[ax] == face) q[ax] = nextafterf(q[ax], INFINITY);
-            }
-        }
+        float q[3], inv[3];
+        table_ray<DIM>(G, V, E, tile, ku, kv, q, inv);
         const int64_t ray = ray_index(G, it.view, ku, kv);
-        if (!waited) {
-            pdl_wait();  // r and the table buffer belong to earlier kernels until here
-            waited = true;
-        }
         *reinterpret_cast<float4*>(dst[k].a) = make_float4(q[0], q[1], inv[0], inv[1]);
         *reinterpret_cast<float4*>(dst[k].b) =
             make_float4(__ldg(a.r + ray), q[2], inv[2], __int_as_float((int)ray));
     }
-    if (!waited) pdl_wait();  // every thread orders the kernel after the previous one
 }
 
 template <int DIM>
@@ -380,12 +407,18 @@ struct alignas(16) ViewCtx2 {
     int rbase;   // table position of bin 0 of the item
 };
 
-// Per-view data of a 3D backprojection CTA.
-struct ViewCtx3 {
-    float S[3], dc[3], eu[3], ev[3];
-    float sdd;
-    int u0, u1, v0, v1;
-    int rbase;   // table position of bin (0, v0) of the item
+// Per-view data of a 3D backprojection CTA: the detector coordinates of its
+// voxel patch, linearised about the patch centre Pc.  For a voxel at Pc + d the
+// candidate window is [w + g . d - h, w + g . d + h] on each detector axis, where
+// h covers the voxel's own shadow anywhere in the patch and the error of the
+// linearisation (see stage_view).
+struct alignas(16) ViewCtx3 {
+    float wu, gu0, gu1, gu2;  // bin coordinate of Pc minus 1/2, and its gradient
+    float wv, gv0, gv1, gv2;
+    float hu, hv;             // window half-widths (bins)
+    int u0, u1, v0, v1;       // bins of the work item
+    int rbase;                // table position of bin (0, v0) of the item
+    int pad[3];
 };
 
 template <int DIM>
@@ -394,7 +427,7 @@ template <>
 struct ViewCtxOf<2> { using type = ViewCtx2; };
 
 __device__ __forceinline__ void stage_view(const DevGeom& G, const DevTile& t, const WorkItem& it,
-                                           ViewCtx2* c) {
+                                           ViewCtx2* c, const float*) {
     const DevView& V = G.views[it.view];
     const bool par = G.kind == PARALLEL_2D;
     c->R0 = (t.T[0] - 0.5f * (float)t.n[0] + 0.5f) - (par ? 0.f : V.S[0]);
@@ -408,17 +441,64 @@ __device__ __forceinline__ void stage_view(const DevGeom& G, const DevTile& t, c
     c->rbase = (int)it.ray_off - it.u0;
 }
 
-__device__ __forceinline__ void stage_view(const DevGeom& G, const DevTile&, const WorkItem& it,
-                                           ViewCtx3* c) {
-    const DevView& V = G.views[it.view];
+// Flat detector (cone beam, custom poses): w(P) = k L / D with D = r . d_c,
+// L = r . e (e = e_u or e_v), r = P - S, k = sdd / pitch.  Its gradient is
+// k (e D - L d_c) / D^2 and the norm of its Hessian is at most
+// k (2 / D^2) (1 + |L| / D).  Over the voxel centres of a 4 x 4 x 4 patch,
+// |P - Pc| <= rho = sqrt(3) 1.5, D >= Dmin = D(Pc) - rho and |L| / D <= T =
+// (|L(Pc)| + rho) / Dmin, so with Hm = k (2 / Dmin^2) (1 + T):
+//   |w(P) - w(Pc) - g . (P - Pc)| <= Hm rho^2 / 2,
+//   the first-order half-width 0.5 sum_k |dw/dP_k| at P is at most its value
+//   at Pc plus 0.5 sqrt(3) Hm rho,
+//   and the second-order widening over a voxel (half diagonal^2 = 3/4) is at
+//   most Hm 3/8.
+// The window half-width adds these to the first-order half-width and the
+// margin; any rounding here only widens or shifts the window by far less than
+// the margin.
+__device__ __forceinline__ void stage_flat_axis(float k, const float r[3], const float dc[3],
+                                                const float e[3], float D, float Dmin, float rho,
+                                                float wbase, float* w, float g[3], float* h) {
+    const float L = r[0] * e[0] + r[1] * e[1] + r[2] * e[2];
+    const float iD = 1.0f / D;
+    *w = fmaf(k * L, iD, wbase);
+    float h1 = 0.f;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        c->S[k] = V.S[k];
-        c->dc[k] = V.dc[k];
-        c->eu[k] = V.eu[k];
-        c->ev[k] = V.ev[k];
+    for (int a = 0; a < 3; ++a) {
+        g[a] = k * (e[a] * D - L * dc[a]) * iD * iD;
+        h1 += fabsf(g[a]);
     }
-    c->sdd = V.sdd;
+    const float T = (fabsf(L) + rho) / Dmin;
+    const float Hm = k * 2.0f / (Dmin * Dmin) * (1.0f + T);
+    *h = 0.5f * h1 + 0.8660254f * Hm * rho + 0.5f * Hm * rho * rho + 0.375f * Hm + kShadowMargin;
+}
+
+__device__ __forceinline__ void stage_view(const DevGeom& G, const DevTile&, const WorkItem& it,
+                                           ViewCtx3* c, const float Pc[3]) {
+    const DevView& V = G.views[it.view];
+    const float rho = 2.5980762f;  // sqrt(3) * 1.5
+    float r[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r[a] = Pc[a] - V.S[a];
+    const float D = r[0] * V.dc[0] + r[1] * V.dc[1] + r[2] * V.dc[2];
+    const float Dmin = D - rho;
+    float g[3];
+    if (Dmin > 1.0f) {
+        stage_flat_axis(V.sdd * G.inv_pu, r, V.dc, V.eu, D, Dmin, rho, fmaf(0.5f, (float)G.nu, -0.5f),
+                        &c->wu, g, &c->hu);
+        c->gu0 = g[0];
+        c->gu1 = g[1];
+        c->gu2 = g[2];
+        stage_flat_axis(V.sdd * G.inv_pv, r, V.dc, V.ev, D, Dmin, rho, fmaf(0.5f, (float)G.nv, -0.5f),
+                        &c->wv, g, &c->hv);
+        c->gv0 = g[0];
+        c->gv1 = g[1];
+        c->gv2 = g[2];
+    } else {
+        // the patch reaches the source's plane: every bin of the item is a candidate
+        c->wu = c->wv = 0.f;
+        c->gu0 = c->gu1 = c->gu2 = c->gv0 = c->gv1 = c->gv2 = 0.f;
+        c->hu = c->hv = 1e30f;
+    }
     c->u0 = it.u0;
     c->u1 = it.u1;
     c->v0 = it.v0;
@@ -472,7 +552,13 @@ __device__ __forceinline__ Cand2 view_cands(const DevGeom& G, const ViewCtx2& c,
         wu = fmaf(lat, G.inv_pu, wbase);
         hu = c.k;
     } else {
-        // first-order shadow, widened for curvature (see voxel_shadow)
+        // The voxel's shadow is [w - h1, w + h1] to first order, h1 = 0.5 sum_k
+        // |dw/dP_k|; the second derivative of a perspective or angular map is at
+        // most ~2 |grad w| / depth, so over half a voxel diagonal (|delta|^2 <=
+        // 3/4) the second-order term is below 1.5 h1 / depth: h = h1 (1 + 1.5 /
+        // depth).  In 2D the two gradient terms are |r1| and |r0| scaled by
+        // 1 / (pitch |r|^2) (curved) or sdd / (pitch depth^2) (flat), since
+        // depth e_u - lat d_c is r turned by 90 degrees.
         const float rd = rcp_approx(depth);
         const float grow = fmaf(1.5f, rd, 1.0f);
         const float l1 = fabsf(r0) + fabsf(r1);  // |d(r . e_u, r . d_c)|_1 terms of grad w
@@ -513,27 +599,16 @@ __device__ __forceinline__ float cand_sum(const Cand2& k, const float lo[3], con
     return s;
 }
 
-// sum over the view's candidate bins of len * r for one voxel (3D)
-__device__ __forceinline__ float view_sum(const DevGeom& G, const ViewCtx3& c, const float P[3],
+// sum over the view's candidate bins of len * r for one voxel (3D); d = P - Pc
+__device__ __forceinline__ float view_sum(const DevGeom&, const ViewCtx3& c, const float d[3],
                                           const float lo[3], const float hi[3],
                                           const RayRec* __restrict__ tab) {
-    DevView V;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        V.S[k] = c.S[k];
-        V.dc[k] = c.dc[k];
-        V.eu[k] = c.eu[k];
-        V.ev[k] = c.ev[k];
-    }
-    V.sdd = c.sdd;
-    float wu, wv, hu, hv;
-    voxel_shadow<3>(G, V, P, &wu, &wv, &hu, &hv);
-    hu += kShadowMargin;
-    hv += kShadowMargin;
-    const int ku0 = max(c.u0, __float2int_ru(wu - 0.5f - hu));
-    const int ku1 = min(c.u1 - 1, __float2int_rd(wu - 0.5f + hu));
-    const int kv0 = max(c.v0, __float2int_ru(wv - 0.5f - hv));
-    const int kv1 = min(c.v1 - 1, __float2int_rd(wv - 0.5f + hv));
+    const float wu = fmaf(c.gu2, d[2], fmaf(c.gu1, d[1], fmaf(c.gu0, d[0], c.wu)));
+    const float wv = fmaf(c.gv2, d[2], fmaf(c.gv1, d[1], fmaf(c.gv0, d[0], c.wv)));
+    const int ku0 = max(c.u0, __float2int_ru(fmaxf(wu - c.hu, -1e9f)));
+    const int ku1 = min(c.u1 - 1, __float2int_rd(fminf(wu + c.hu, 1e9f)));
+    const int kv0 = max(c.v0, __float2int_ru(fmaxf(wv - c.hv, -1e9f)));
+    const int kv1 = min(c.v1 - 1, __float2int_rd(fminf(wv + c.hv, 1e9f)));
     const int wdt = c.u1 - c.u0;
     const RayRec* base = tab + c.rbase - c.v0 * wdt;  // + kv * wdt + ku
     // the first 2 x 2 candidates without branches (bins clamped into the item,
@@ -588,6 +663,12 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
     const int x2 = DIM == 3 ? (b12 / nb1) * 4 + lv / (P0 * P1) : 0;
     const bool valid = x0 < t.n[0] && x1 < t.n[1] && x2 < t.n[2];
     const int v = (x2 * t.n[1] + x1) * t.n[0] + x0;  // tile-local voxel index
+    // 3D: patch centre (tile-centred) and this voxel's offset from it
+    const float Pc[3] = {-0.5f * (float)t.n[0] + (float)(b0 * P0) + 2.0f + t.T[0],
+                         -0.5f * (float)t.n[1] + (float)((b12 % nb1) * P1) + 2.0f + t.T[1],
+                         -0.5f * (float)t.n[2] + (float)((b12 / nb1) * 4) + 2.0f + t.T[2]};
+    const float dP[3] = {(float)(lv % P0) - 1.5f, (float)((lv / P0) % P1) - 1.5f,
+                         (float)(lv / (P0 * P1)) - 1.5f};
     // voxel box [lo, hi) in tile-centred coordinates, centre P
     float lo[3], hi[3], P[3];
     lo[0] = -0.5f * (float)t.n[0] + (float)x0;
@@ -605,7 +686,7 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
         const int nb = min(kViewBatch, n_items - base);
         __syncthreads();
         for (int k = threadIdx.x; k < nb; k += blockDim.x)
-            stage_view(G, t, items[sd.w0 + base + k], &vs[k]);
+            stage_view(G, t, items[sd.w0 + base + k], &vs[k], Pc);
         __syncthreads();
         if (base == 0) pdl_wait();  // the ray table is the previous kernel's
         if (!valid) continue;
@@ -623,7 +704,7 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
             }
             for (; i < nb; i += C) acc.add(cand_sum(view_cands(G, vs[i], (float)x0, (float)x1, tab), lo, hi));
         } else {
-            for (int i = chunk; i < nb; i += C) acc.add(view_sum(G, vs[i], P, lo, hi, tab));
+            for (int i = chunk; i < nb; i += C) acc.add(view_sum(G, vs[i], dP, lo, hi, tab));
         }
     }
     if (n_items <= 0) pdl_wait();
