@@ -271,6 +271,29 @@ int32_t csgd_solve(csgd_solver* solver, int64_t n_steps, float* x_out, int32_t x
 int32_t csgd_solver_history(csgd_solver* solver, csgd_step_info* out, int64_t capacity,
                             int64_t* count);
 
+/* Checkpoint and resume (the paper has no counterpart: the paper's runs are
+ * short; long or preemptible runs need it).  The state of a solver is its whole
+ * iteration state: y, x, x^, the per-tile candidate counts, r, the z store, the
+ * pending refresh of epoch sync, the schedule's generator state and the rest of
+ * the current epoch's schedule, the counters (epochs, steps, non-zeros) and the
+ * per-step history.  It is written to a caller-owned host buffer in a
+ * versioned, self-describing layout (little-endian, as the host writes it).
+ *   csgd_solver_state_bytes: size of the state of this solver, in bytes.
+ *   csgd_solver_get_state: writes the state to buf (capacity bytes, at least
+ *     csgd_solver_state_bytes); synchronises the stream.  CSGD_ERR_INVALID_ARG
+ *     if the buffer is too small.
+ *   csgd_solver_set_state: restores a state written by csgd_solver_get_state of
+ *     a solver on an equal partition (same sizes) with equal parameters; the run
+ *     then continues exactly as the saved one would have.  Synchronises the
+ *     stream.  CSGD_ERR_STATE if the buffer is not such a state (bad magic or
+ *     version, other sizes or parameters, truncated); the solver is unchanged
+ *     then. */
+int32_t csgd_solver_state_bytes(const csgd_solver* solver, int64_t* bytes);
+int32_t csgd_solver_get_state(csgd_solver* solver, void* buf, int64_t capacity,
+                              csgd_stream stream);
+int32_t csgd_solver_set_state(csgd_solver* solver, const void* buf, int64_t size,
+                              csgd_stream stream);
+
 /* ---------------------------------------------------------------------------
  * Solves as CUDA graphs, and many solves in one launch
  * (the paper has no counterpart: these serve batched and repeated solves)

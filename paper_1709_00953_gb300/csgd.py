@@ -107,6 +107,9 @@ SIGNATURES = {
     "csgd_solve_step": ([_vp, ctypes.POINTER(BlockChoice), ctypes.POINTER(StepInfo), _vp], _i32),
     "csgd_solve": ([_vp, _i64, _vp, _i32, ctypes.POINTER(Report), _i32, _vp], _i32),
     "csgd_solver_history": ([_vp, ctypes.POINTER(StepInfo), _i64, ctypes.POINTER(_i64)], _i32),
+    "csgd_solver_state_bytes": ([_vp, ctypes.POINTER(_i64)], _i32),
+    "csgd_solver_get_state": ([_vp, _vp, _i64, _vp], _i32),
+    "csgd_solver_set_state": ([_vp, _vp, _i64, _vp], _i32),
     "csgd_solver_graph_create": ([_vp, _i64, _vp, _i32, ctypes.POINTER(_vp)], _i32),
     "csgd_graph_batch_create": ([ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp)], _i32),
     "csgd_graph_launch": ([_vp, _vp], _i32),
@@ -412,6 +415,19 @@ class Solver:
         h = ctypes.c_void_p()
         _check(load().csgd_solver_graph_create(self.handle, int(n_steps), ptr, host, ctypes.byref(h)))
         return Graph(h, [self, x_out])
+
+    def state(self, stream=None) -> np.ndarray:
+        """Checkpoint: the solver's whole iteration state as a host byte array."""
+        n = ctypes.c_int64()
+        _check(load().csgd_solver_state_bytes(self.handle, ctypes.byref(n)))
+        buf = np.zeros(int(n.value), dtype=np.uint8)
+        _check(load().csgd_solver_get_state(self.handle, buf.ctypes.data, buf.size, _stream(stream)))
+        return buf
+
+    def set_state(self, buf, stream=None):
+        """Resume from a checkpoint taken by state() (same partition and parameters)."""
+        arr = np.ascontiguousarray(np.asarray(buf, dtype=np.uint8))
+        _check(load().csgd_solver_set_state(self.handle, arr.ctypes.data, arr.size, _stream(stream)))
 
     def profile(self, enable: bool = True):
         _check(load().csgd_solver_profile(self.handle, int(bool(enable))))

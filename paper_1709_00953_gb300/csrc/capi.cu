@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <new>
@@ -1194,3 +1195,208 @@ int32_t csgd_solver_profile_read(csgd_solver* S, csgd_kernel_times* out, int32_t
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// checkpoint and resume
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char kStateMagic[8] = {'C', 'S', 'G', 'D', 'S', 'T', 'A', 'T'};
+constexpr int32_t kStateVersion = 1;
+
+struct StateHeader {
+    char magic[8];
+    int32_t version;
+    int32_t has_d;            // the pending refresh d of epoch sync follows r
+    int64_t n_rays, n_vox, n_tiles, z_floats;
+    int64_t hist_rows;        // history rows stored
+    int64_t queue_len;        // queued steps of the current epoch
+    int64_t queue_ints;       // int32 values of the queue section
+    csgd_solver_params prm;   // must equal the restoring solver's
+    uint64_t rng_state;
+    int64_t epoch, steps_done;
+    int32_t epoch_open, last_group;
+    uint64_t nnz;             // non-zeros counted since the last reset
+};
+
+int64_t align8(int64_t n) { return (n + 7) & ~(int64_t)7; }
+
+// Section sizes of a solver's state, in the order they are written.
+struct StateLayout {
+    int64_t queue_ints = 0, hist_rows = 0;
+    int64_t off_queue = 0, off_y = 0, off_x = 0, off_xh = 0, off_r = 0, off_z = 0, off_d = 0,
+            off_cnt = 0, off_hist = 0, total = 0;
+};
+
+StateLayout state_layout(const csgd_solver* S, int64_t queue_ints, int64_t hist_rows, bool has_d) {
+    const Partition& p = S->P->p;
+    StateLayout L;
+    L.queue_ints = queue_ints;
+    L.hist_rows = hist_rows;
+    int64_t o = align8(sizeof(StateHeader));
+    L.off_queue = o;
+    o = align8(o + 4 * queue_ints);
+    L.off_y = o;
+    o = align8(o + 4 * S->n_rays);
+    L.off_x = o;
+    o = align8(o + 4 * S->n_vox);
+    L.off_xh = o;
+    o = align8(o + 4 * S->n_vox);
+    L.off_r = o;
+    o = align8(o + 4 * S->n_rays);
+    L.off_z = o;
+    o = align8(o + 4 * std::max<int64_t>(0, p.z_floats));
+    L.off_d = o;
+    o = align8(o + (has_d ? 4 * S->n_rays : 0));
+    L.off_cnt = o;
+    o = align8(o + 4 * (int64_t)p.n);
+    L.off_hist = o;
+    o = align8(o + 8 * kHistCols * hist_rows);
+    L.total = o;
+    return L;
+}
+
+int64_t queue_int_count(const csgd_solver* S) {
+    int64_t n = 0;
+    for (const QueuedStep& q : S->queue) n += 3 + (int64_t)q.group.size();
+    return n;
+}
+
+bool same_params(const csgd_solver_params& a, const csgd_solver_params& b) {
+    return a.sampling == b.sampling && a.sync == b.sync && a.group_size == b.group_size &&
+           a.alpha == b.alpha && a.gamma == b.gamma && a.b == b.b &&
+           a.theta_step == b.theta_step && a.seed == b.seed;
+}
+
+}  // namespace
+
+int32_t csgd_solver_state_bytes(const csgd_solver* S, int64_t* bytes) {
+    if (!S || !bytes) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    const int64_t rows = std::min<int64_t>(S->steps_done, S->sb.hist_cap);
+    *bytes = state_layout(S, queue_int_count(S), rows, S->prm.sync == CSGD_SYNC_EPOCH).total;
+    return CSGD_OK;
+}
+
+int32_t csgd_solver_get_state(csgd_solver* S, void* buf, int64_t capacity, csgd_stream stream) {
+    if (!S || !buf) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Partition& p = S->P->p;
+    const bool has_d = S->prm.sync == CSGD_SYNC_EPOCH;
+    const int64_t rows = std::min<int64_t>(S->steps_done, S->sb.hist_cap);
+    const StateLayout L = state_layout(S, queue_int_count(S), rows, has_d);
+    if (capacity < L.total) return fail(CSGD_ERR_INVALID_ARG, "state buffer too small");
+    char* out = (char*)buf;
+    std::memset(out, 0, (size_t)L.total);
+    StateHeader h{};
+    std::memcpy(h.magic, kStateMagic, 8);
+    h.version = kStateVersion;
+    h.has_d = has_d ? 1 : 0;
+    h.n_rays = S->n_rays;
+    h.n_vox = S->n_vox;
+    h.n_tiles = p.n;
+    h.z_floats = p.z_floats;
+    h.hist_rows = rows;
+    h.queue_len = (int64_t)S->queue.size();
+    h.queue_ints = L.queue_ints;
+    h.prm = S->prm;
+    h.rng_state = S->rng.state;
+    h.epoch = S->epoch;
+    h.steps_done = S->steps_done;
+    h.epoch_open = S->epoch_open ? 1 : 0;
+    h.last_group = S->last_group;
+    unsigned long long nnz = 0;
+    CSGD_CUDA(cudaMemcpyAsync(&nnz, S->sb.nnz, sizeof(nnz), cudaMemcpyDeviceToHost, s), "read nnz");
+    int32_t* qi = (int32_t*)(out + L.off_queue);
+    for (const QueuedStep& q : S->queue) {
+        *qi++ = q.j;
+        *qi++ = (int32_t)q.group.size();
+        *qi++ = q.last_in_batch ? 1 : 0;
+        for (int g : q.group) *qi++ = g;
+    }
+    auto d2h = [&](int64_t off, const void* src, int64_t bytes, const char* what) {
+        if (bytes <= 0) return cudaSuccess;
+        cudaError_t e = cudaMemcpyAsync(out + off, src, (size_t)bytes, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) fail(CSGD_ERR_CUDA, what);
+        return e;
+    };
+    if (d2h(L.off_y, S->sb.y, 4 * S->n_rays, "read y") != cudaSuccess ||
+        d2h(L.off_x, S->sb.x, 4 * S->n_vox, "read x") != cudaSuccess ||
+        d2h(L.off_xh, S->sb.xh, 4 * S->n_vox, "read x^") != cudaSuccess ||
+        d2h(L.off_r, S->sb.r, 4 * S->n_rays, "read r") != cudaSuccess ||
+        d2h(L.off_z, S->sb.z, 4 * p.z_floats, "read z") != cudaSuccess ||
+        (has_d && d2h(L.off_d, S->sb.d, 4 * S->n_rays, "read d") != cudaSuccess) ||
+        d2h(L.off_cnt, S->sb.cnt, 4 * (int64_t)p.n, "read counts") != cudaSuccess ||
+        d2h(L.off_hist, S->sb.hist, 8 * kHistCols * rows, "read history") != cudaSuccess)
+        return CSGD_ERR_CUDA;
+    CSGD_CUDA(cudaStreamSynchronize(s), "state sync");
+    h.nnz = nnz;
+    std::memcpy(out, &h, sizeof(h));
+    return CSGD_OK;
+}
+
+int32_t csgd_solver_set_state(csgd_solver* S, const void* buf, int64_t size, csgd_stream stream) {
+    if (!S || !buf) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Partition& p = S->P->p;
+    if (size < (int64_t)sizeof(StateHeader)) return fail(CSGD_ERR_STATE, "not a solver state");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != kStateVersion)
+        return fail(CSGD_ERR_STATE, "not a solver state of this version");
+    const bool has_d = S->prm.sync == CSGD_SYNC_EPOCH;
+    if (h.n_rays != S->n_rays || h.n_vox != S->n_vox || h.n_tiles != p.n ||
+        h.z_floats != p.z_floats || (h.has_d != 0) != has_d)
+        return fail(CSGD_ERR_STATE, "state of a solver with other sizes");
+    if (!same_params(h.prm, S->prm)) return fail(CSGD_ERR_STATE, "state of a solver with other parameters");
+    if (h.hist_rows < 0 || h.hist_rows > h.steps_done || h.queue_len < 0 || h.queue_ints < 3 * h.queue_len)
+        return fail(CSGD_ERR_STATE, "corrupt state header");
+    const StateLayout L = state_layout(S, h.queue_ints, h.hist_rows, has_d);
+    if (size < L.total) return fail(CSGD_ERR_STATE, "truncated solver state");
+    // the queued schedule, checked before anything is changed
+    const char* in = (const char*)buf;
+    const int32_t* qi = (const int32_t*)(in + L.off_queue);
+    const int32_t* qe = qi + h.queue_ints;
+    std::deque<QueuedStep> queue;
+    for (int64_t k = 0; k < h.queue_len; ++k) {
+        if (qe - qi < 3) return fail(CSGD_ERR_STATE, "corrupt schedule section");
+        QueuedStep q;
+        q.j = qi[0];
+        const int32_t ng = qi[1];
+        q.last_in_batch = qi[2] != 0;
+        qi += 3;
+        if (q.j < 0 || q.j >= p.n || ng < 0 || ng > p.m || qe - qi < ng)
+            return fail(CSGD_ERR_STATE, "corrupt schedule section");
+        for (int32_t g = 0; g < ng; ++g) {
+            if (qi[g] < 0 || qi[g] >= p.m) return fail(CSGD_ERR_STATE, "corrupt schedule section");
+            q.group.push_back(qi[g]);
+        }
+        qi += ng;
+        queue.push_back(std::move(q));
+    }
+    int rc = ensure_history(S, std::max<int64_t>(h.hist_rows, 1), s);
+    if (rc) return rc;
+    auto h2d = [&](void* dst, int64_t off, int64_t bytes) {
+        if (bytes <= 0) return cudaSuccess;
+        return cudaMemcpyAsync(dst, in + off, (size_t)bytes, cudaMemcpyHostToDevice, s);
+    };
+    const unsigned long long nnz = h.nnz;
+    cudaError_t e = h2d((void*)S->sb.y, L.off_y, 4 * S->n_rays);
+    if (e == cudaSuccess) e = h2d(S->sb.x, L.off_x, 4 * S->n_vox);
+    if (e == cudaSuccess) e = h2d(S->sb.xh, L.off_xh, 4 * S->n_vox);
+    if (e == cudaSuccess) e = h2d(S->sb.r, L.off_r, 4 * S->n_rays);
+    if (e == cudaSuccess) e = h2d(S->sb.z, L.off_z, 4 * p.z_floats);
+    if (e == cudaSuccess && has_d) e = h2d(S->sb.d, L.off_d, 4 * S->n_rays);
+    if (e == cudaSuccess) e = h2d(S->sb.cnt, L.off_cnt, 4 * (int64_t)p.n);
+    if (e == cudaSuccess) e = h2d(S->sb.hist, L.off_hist, 8 * kHistCols * h.hist_rows);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->sb.nnz, &nnz, sizeof(nnz), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "restore solver state");
+    S->rng.state = h.rng_state;
+    S->epoch = h.epoch;
+    S->steps_done = h.steps_done;
+    S->epoch_open = h.epoch_open != 0;
+    S->last_group = h.last_group;
+    S->queue = std::move(queue);
+    return CSGD_OK;
+}
