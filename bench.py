@@ -396,8 +396,19 @@ def run_gpu(args, cfg, world, rank, local):
         res = oracle_sample(cfg, y, seconds=args.cpu_seconds)
         cpu = {"value": 3.0 * res["nnz"] / res["seconds"], "unit": "updates/s",
                "cores": res["cores"], "kind": "oracle",
+               "steps_per_s": res["steps"] / res["seconds"],
                "sample": "first %d block steps of %s (%.1f s of FP64 oracle work)"
                          % (res["steps"], cfg["name"], res["seconds"])}
+        # the same oracle on one host core, a shorter sample
+        from oracle import siddon
+        n_all = siddon.num_threads()
+        siddon.set_threads(1)
+        try:
+            one = oracle_sample(cfg, y, seconds=args.cpu_seconds / 3)
+        finally:
+            siddon.set_threads(n_all)
+        cpu["value_1core"] = 3.0 * one["nnz"] / one["seconds"]
+        cpu["sample_1core"] = "first %d block steps (%.1f s)" % (one["steps"], one["seconds"])
 
     line = {
         "metric": "ray-voxel updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
