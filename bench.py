@@ -16,6 +16,7 @@ Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|refere
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import math
 import os
@@ -452,7 +453,9 @@ def run_batch(args, world, rank, local):
     from paper_1709_00953_gb300 import batch
     cfgs = C.batch_fan2d()
     probs = [batch.Problem(c, D.make_data(c, device="cuda")[0]) for c in cfgs]
-    b = batch.Batch(probs)
+    t_tune = time.perf_counter()
+    b = batch.Batch(probs, autotune=True)
+    t_tune = time.perf_counter() - t_tune
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -506,6 +509,9 @@ def run_batch(args, world, rank, local):
         "speedup_vs_one_by_one": ms_1 / ms_b,
         "updates_per_s": 3.0 * nnz * args.steps / (ms_b / 1e3),
         "identical_results": same,
+        "launch_shapes": {"autotuned": True, "seconds": t_tune,
+                          "view_groups": sorted(collections.Counter(p.shapes[0] for p in probs).items()),
+                          "lanes_per_ray": sorted(collections.Counter(p.shapes[1] for p in probs).items())},
     }
     if ck:
         line["clocks"] = ck

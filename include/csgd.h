@@ -318,6 +318,21 @@ int32_t csgd_graph_batch_create(csgd_graph* const* parts, int32_t n, csgd_graph*
 int32_t csgd_graph_launch(csgd_graph* graph, csgd_stream stream);
 int32_t csgd_graph_destroy(csgd_graph* graph);
 
+/* Launch shapes (the paper has no counterpart: these tune the GPU kernels, not
+ * the method).  bp_groups = view groups per backprojection CTA (1..8) and
+ * fwd_lanes = lanes per ray of the dual forward (1, 2 or 4); 0 selects the
+ * library's model (occupancy-based groups, lanes by ray count).  They change
+ * only the order of FP32 partial sums, i.e. results at rounding level.
+ *   csgd_solver_set_launch: sets them; CSGD_ERR_INVALID_ARG out of range.
+ *   csgd_solver_autotune: times the backprojection for every group count and
+ *     then the dual forward for every lane count over the first trial_steps
+ *     steps of the schedule (kernel time by CUDA events), keeps the fastest
+ *     and resets the solver (x = 0, z = 0, r = y, schedule from the seed);
+ *     writes the choice to bp_groups / fwd_lanes if non-NULL.  Synchronises. */
+int32_t csgd_solver_set_launch(csgd_solver* solver, int32_t bp_groups, int32_t fwd_lanes);
+int32_t csgd_solver_autotune(csgd_solver* solver, int64_t trial_steps, int32_t* bp_groups,
+                             int32_t* fwd_lanes, csgd_stream stream);
+
 /* Per-kernel timing (the paper has no counterpart; it supports the roofline
  * measurements).  While enabled, every kernel launch of csgd_solve /
  * csgd_solve_step is bracketed by CUDA events on the caller's stream.

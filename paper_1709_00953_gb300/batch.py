@@ -2,7 +2,8 @@
 
 Each problem keeps its own geometry, partition and solver state on the device.
 Every problem's whole solve (reset, all block steps, epoch averages, x out) is
-captured once into a CUDA graph; the batch is a graph whose child graphs are
+captured once into a CUDA graph, optionally after its kernel launch shapes are
+autotuned for its sizes; the batch is a graph whose child graphs are
 those solves, with no dependencies between them, so one launch runs all block
 steps of all problems and the GPU overlaps the small ones.  Results are the
 same as solving each problem alone: the kernels are deterministic and the
@@ -28,6 +29,14 @@ class Problem:
         self.steps = int(cfg["steps"])
         self._graph = None
 
+    def autotune(self, trial_steps: int | None = None) -> tuple:
+        """Picks this problem's kernel launch shapes by timing them (before its graph
+        is captured); returns (view groups, lanes per ray)."""
+        if self._graph is not None:
+            raise RuntimeError("autotune before the graph is captured")
+        self.shapes = self.solver.autotune(trial_steps or min(self.steps, 16))
+        return self.shapes
+
     def graph(self) -> csgd.Graph:
         if self._graph is None:
             self._graph = self.solver.graph(self.steps, self.x)
@@ -42,8 +51,11 @@ class Problem:
 class Batch:
     """A set of problems and the single graph that solves all of them."""
 
-    def __init__(self, problems):
+    def __init__(self, problems, autotune: bool = False):
         self.problems = list(problems)
+        if autotune:
+            for p in self.problems:
+                p.autotune()
         self.graph = csgd.graph_batch([p.graph() for p in self.problems])
 
     def launch(self, stream=None):

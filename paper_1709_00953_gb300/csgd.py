@@ -108,6 +108,8 @@ SIGNATURES = {
     "csgd_solve": ([_vp, _i64, _vp, _i32, ctypes.POINTER(Report), _i32, _vp], _i32),
     "csgd_solver_history": ([_vp, ctypes.POINTER(StepInfo), _i64, ctypes.POINTER(_i64)], _i32),
     "csgd_solver_state_bytes": ([_vp, ctypes.POINTER(_i64)], _i32),
+    "csgd_solver_set_launch": ([_vp, _i32, _i32], _i32),
+    "csgd_solver_autotune": ([_vp, _i64, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _vp], _i32),
     "csgd_solver_get_state": ([_vp, _vp, _i64, _vp], _i32),
     "csgd_solver_set_state": ([_vp, _vp, _i64, _vp], _i32),
     "csgd_solver_graph_create": ([_vp, _i64, _vp, _i32, ctypes.POINTER(_vp)], _i32),
@@ -415,6 +417,18 @@ class Solver:
         h = ctypes.c_void_p()
         _check(load().csgd_solver_graph_create(self.handle, int(n_steps), ptr, host, ctypes.byref(h)))
         return Graph(h, [self, x_out])
+
+    def set_launch(self, bp_groups: int = 0, fwd_lanes: int = 0):
+        """Launch shapes of the kernels (0 = the library's models)."""
+        _check(load().csgd_solver_set_launch(self.handle, int(bp_groups), int(fwd_lanes)))
+
+    def autotune(self, trial_steps: int, stream=None) -> tuple:
+        """Times every launch shape over the first trial_steps steps, keeps the
+        fastest and resets the solver; returns (bp_groups, fwd_lanes)."""
+        c, l = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().csgd_solver_autotune(self.handle, int(trial_steps), ctypes.byref(c),
+                                           ctypes.byref(l), _stream(stream)))
+        return c.value, l.value
 
     def state(self, stream=None) -> np.ndarray:
         """Checkpoint: the solver's whole iteration state as a host byte array."""

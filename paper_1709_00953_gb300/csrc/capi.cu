@@ -203,6 +203,8 @@ struct csgd_solver {
     bool epoch_open = false;        // candidates accumulated since the last close
     int max_slots = 1;
     int last_group = 0;             // row blocks of the last planned step
+    int bp_groups = 0;              // launch shapes (0: the library's models)
+    int fwd_lanes = 0;
     int64_t max_rays_per_step = 0;
     // device arrays for the schedule of one solve call
     WorkItem* d_items = nullptr;
@@ -469,6 +471,8 @@ int launch_plan(csgd_solver* S, Plan& pl, cudaStream_t s) {
                 b.max_item_rays,
                 (int64_t)(pl.items[w].u1 - pl.items[w].u0) * (pl.items[w].v1 - pl.items[w].v0));
         b.sync_epoch = S->prm.sync == CSGD_SYNC_EPOCH;
+        b.bp_groups = S->bp_groups;
+        b.fwd_lanes = S->fwd_lanes;
         cudaEvent_t evs[4];
         int e0 = 0;
         if (S->profiling) {
@@ -1398,5 +1402,82 @@ int32_t csgd_solver_set_state(csgd_solver* S, const void* buf, int64_t size, csg
     S->epoch_open = h.epoch_open != 0;
     S->last_group = h.last_group;
     S->queue = std::move(queue);
+    return CSGD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch shapes and their autotuning
+// ---------------------------------------------------------------------------
+int32_t csgd_solver_set_launch(csgd_solver* S, int32_t bp_groups, int32_t fwd_lanes) {
+    if (!S) return fail(CSGD_ERR_INVALID_ARG, "NULL solver");
+    if (bp_groups < 0 || bp_groups > kBPMaxChunks)
+        return fail(CSGD_ERR_INVALID_ARG, "view groups must be 0 (model) or 1..8");
+    if (fwd_lanes != 0 && fwd_lanes != 1 && fwd_lanes != 2 && fwd_lanes != 4)
+        return fail(CSGD_ERR_INVALID_ARG, "lanes per ray must be 0 (model), 1, 2 or 4");
+    S->bp_groups = bp_groups;
+    S->fwd_lanes = fwd_lanes;
+    return CSGD_OK;
+}
+
+namespace {
+// Device time of the backprojection (kind 0) or dual forward (kind 1) kernels
+// over the first `steps` scheduled steps from a fresh state.
+int trial_ms(csgd_solver* S, int64_t steps, int kind, cudaStream_t s, double* ms) {
+    int rc = solver_reset_state(S, s);
+    if (rc) return rc;
+    rc = csgd_solver_profile(S, 1);
+    if (rc) return rc;
+    csgd_kernel_times t{};
+    csgd_solver_profile_read(S, &t, 1);
+    Plan pl;
+    plan_scheduled(S, &pl, steps, false);
+    rc = execute_plan(S, pl, s);
+    if (rc == CSGD_OK) rc = csgd_solver_profile_read(S, &t, 1);
+    csgd_solver_profile(S, 0);
+    if (rc) return rc;
+    *ms = t.ms[kind];
+    return CSGD_OK;
+}
+}  // namespace
+
+int32_t csgd_solver_autotune(csgd_solver* S, int64_t trial_steps, int32_t* bp_groups,
+                             int32_t* fwd_lanes, csgd_stream stream) {
+    if (!S || trial_steps <= 0) return fail(CSGD_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    double ms = 0.0;
+    S->bp_groups = 0;
+    S->fwd_lanes = 0;
+    int rc = trial_ms(S, trial_steps, 0, s, &ms);  // warm-up (module loading, caches)
+    int best_c = 0;
+    double best = 0.0;
+    for (int c = 1; rc == CSGD_OK && c <= kBPMaxChunks; ++c) {
+        S->bp_groups = c;
+        rc = trial_ms(S, trial_steps, 0, s, &ms);
+        if (rc == CSGD_OK && (best_c == 0 || ms < best)) {
+            best = ms;
+            best_c = c;
+        }
+    }
+    S->bp_groups = best_c;
+    int best_l = 0;
+    for (int l = 1; rc == CSGD_OK && l <= 4; l *= 2) {
+        S->fwd_lanes = l;
+        rc = trial_ms(S, trial_steps, 1, s, &ms);
+        if (rc == CSGD_OK && (best_l == 0 || ms < best)) {  // l = 1 starts the comparison
+            best = ms;
+            best_l = l;
+        }
+    }
+    if (rc != CSGD_OK) {
+        S->bp_groups = S->fwd_lanes = 0;
+        solver_reset_state(S, s);
+        return rc;
+    }
+    S->fwd_lanes = best_l;
+    rc = solver_reset_state(S, s);
+    if (rc) return rc;
+    CSGD_CUDA(cudaStreamSynchronize(s), "autotune sync");
+    if (bp_groups) *bp_groups = S->bp_groups;
+    if (fwd_lanes) *fwd_lanes = S->fwd_lanes;
     return CSGD_OK;
 }

@@ -28,7 +28,6 @@ namespace {
 
 constexpr int kFwdThreads = 256;
 constexpr int kFwdBatch = 4;  // crossings per batch of gathers in the dual forward
-constexpr int kBPMaxChunks = 8;
 constexpr int kBPMaxThreads = kBPVox * kBPMaxChunks;
 constexpr int kEpiThreads = 256;
 
@@ -921,7 +920,7 @@ static int bp_resident(int dim, int C) {
 }
 
 BPPlan plan_backprojection(const DevGeom& G, const DevTile& tile, int nslots, int views,
-                           int sm_count) {
+                           int sm_count, int force_groups) {
     // Estimated time for C view groups: (waves of CTAs) x (views per thread +
     // a fixed cost of staging, counted as 4 views) / (issue efficiency, taken
     // as proportional to resident warps below 32 per SM).  Ties go to the
@@ -945,6 +944,7 @@ BPPlan plan_backprojection(const DevGeom& G, const DevTile& tile, int nslots, in
         }
         if (views <= C) break;
     }
+    if (force_groups >= 1 && force_groups <= kBPMaxChunks) p.C = force_groups;
     return p;
 }
 
@@ -1085,7 +1085,7 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
                          int sm_count, cudaStream_t s, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], s);
     BPPlan plan = plan_backprojection(G, tile, b.nslots, (b.n_items + b.nslots - 1) / b.nslots,
-                                      sm_count);
+                                      sm_count, b.bp_groups);
     // 1. g_J = (A_I^J)^T r_I per slot: ray table, then voxel-driven sums
     TableArgs ta;
     ta.G = G;
@@ -1121,7 +1121,8 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     f.sync_epoch = b.sync_epoch;
     f.n_gg = plan.blocks;
     f.sb = sb;
-    const int L = lanes_per_ray(b.max_rays * b.nslots, sm_count);
+    const int L = b.fwd_lanes == 1 || b.fwd_lanes == 2 || b.fwd_lanes == 4
+                      ? b.fwd_lanes : lanes_per_ray(b.max_rays * b.nslots, sm_count);
     int64_t nb = (b.max_rays * L + kFwdThreads - 1) / kFwdThreads;
     if (nb < 1) nb = 1;
     if (nb > sb.max_fwd_blocks || nb > sb.qq_stride) return cudaErrorInvalidValue;

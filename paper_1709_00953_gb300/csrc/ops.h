@@ -23,6 +23,7 @@ struct InlineItems {
 // voxels of the tile (8 x 8 in 2D, 4 x 4 x 4 in 3D) with its views split among
 // C thread groups of kBPVox threads.
 constexpr int kBPVox = 64;
+constexpr int kBPMaxChunks = 8;  // view groups per CTA at most
 inline int bp_patch(int dim, int axis) { return dim == 2 ? (axis < 2 ? 8 : 1) : 4; }
 inline int bp_blocks(const DevTile& t, int dim) {
     int b = 1;
@@ -34,7 +35,7 @@ struct BPPlan {
     int C;       // view groups per CTA
 };
 BPPlan plan_backprojection(const DevGeom& G, const DevTile& tile, int nslots, int views,
-                           int sm_count);
+                           int sm_count, int force_groups = 0);
 
 // ---- stand-alone operators (inline items, one slot) -------------------------
 // out[ray] = (accumulate ? out[ray] : 0) + h * sum A x over the items' rays.
@@ -95,6 +96,8 @@ struct BatchLaunch {
     int w_begin, n_items;    // work items of the batch (contiguous)
     int64_t max_item_rays;   // rays of the largest work item
     int sync_epoch;
+    int bp_groups = 0;       // view groups per backprojection CTA (0: occupancy model)
+    int fwd_lanes = 0;       // lanes per ray of the dual forward (0: by ray count)
 };
 
 // ev (optional, 4 events): recorded before the backprojection, after it, after
