@@ -420,7 +420,9 @@ def run_gpu(args, cfg, world, rank, local):
                    "nnz_per_solve": int(nnz_per_solve), "n_rays": int(p.n_rays),
                    "n_voxels": int(p.n_voxels), "l2": "flushed (256 MB write) before each step",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "solves_per_s": 1e3 * args.steps * world / ms},
+                   "solves_per_s": 1e3 * args.steps * world / ms,
+                   "epochs_per_solve": int(rep["epochs"]),
+                   "ms_per_epoch": ms / args.steps / max(1, int(rep["epochs"]))},
         "roofline": roof, "kernels": kernels, "gpu_launches": launches,
         "launch": "one CUDA graph per solve (reset, all block steps, epoch averages)",
         "kernel_timing": "per-launch CUDA events in a second pass of the same %d solves launched "
