@@ -1,11 +1,11 @@
-// Device helpers: ray set-up (a1) and incremental Siddon traversal.
+// Device helpers: ray set-up (a1), incremental Siddon traversal (the forward
+// products) and small reductions.
 //
-// A_i^j is the length of line i inside voxel j (Sec. II-A).  Every kernel that
-// needs entries of A calls `traverse` with a box of voxels (a whole tile for the
-// forward products, a shared-memory sub-box for the backprojection), so the
-// forward and adjoint operators see bit-identical lengths for the same line and
-// plane: the crossing parameter of a plane is always t = (plane - q) / d
-// evaluated the same way, in tile-centred coordinates.
+// A_i^j is the length of line i inside voxel j (Sec. II-A).  The forward walks
+// and the voxel-driven backprojection's slab clip both evaluate the crossing
+// parameter of a plane as t = (plane - q) * (1/d) in tile-centred coordinates,
+// with the same operations, so the forward and adjoint operators see
+// bit-identical lengths for the same line and voxel.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -313,13 +313,6 @@ __device__ __forceinline__ int walk3_batched(const float q[3], const float inv[3
     return cnt;
 }
 
-template <int DIM, class F>
-__device__ __forceinline__ int traverse(const float q[3], const float inv[3], const Box& b, F&& f) {
-    float tin, tout;
-    if (!clip<DIM>(q, inv, b, &tin, &tout)) return 0;
-    return walk<DIM>(q, inv, b, tin, tout, f);
-}
-
 // Programmatic dependent launch.  pdl_trigger lets the next kernel of the
 // stream (launched with programmatic stream serialization) be scheduled while
 // this one runs; pdl_wait blocks until the previous kernel of the stream has
@@ -352,7 +345,8 @@ __device__ __forceinline__ float atan_series(float x) {
     return x * p;
 }
 
-// Compensated (Kahan) accumulator for the FP32 ray sums.
+// Compensated (Kahan) accumulator: the stand-alone projection's ray sums and
+// the backprojection's per-voxel sums over views.
 struct Kahan {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float v) {

@@ -1,23 +1,28 @@
 // Siddon block operators and the solver's per-batch kernels (sm_103a).
 //
-//   k_forward      z_I = A_I^J x_J (one vector) or, in the solver, p = A x_J and
-//                  q = A g_J in one traversal with ||q||^2 in FP64 and the step
-//                  length mu computed by the last CTA (Alg. 1, Eq. 'step').
-//   k_ray_table    per launch, the line (tile-centred point q, 1/d) and the
-//                  residual r of every ray of every slot, set up once.
-//   k_backproject  g_J = (A_I^J)^T r_I (Eq. 'direction'): voxel-driven gather over
-//                  the ray table (each voxel sums len * r over the bins of its
-//                  shadow), the partial sums of a CTA's view groups added in
-//                  shared memory in a fixed order, g^T g in FP64.  No atomics.
-//   k_epilogue     z_I^j = p + mu q, r -= z_new - z_old (the refresh of Alg. 2-4
-//                  applied incrementally), x^_J += x_J + mu g_J.
-//   k_average      x_J = x^_J / count_J at the end of an epoch.
+//   k_project_inline  z_I = A_I^J x_J for the stand-alone operator: ray-driven
+//                     incremental walk, 1-4 lanes per ray.
+//   k_ray_table_*     per launch, the line (tile-centred point q, 1/d) and the
+//                     residual r of every ray of every slot, set up once.
+//   k_backproject_*   g_J = (A_I^J)^T r_I (Eq. 'direction'): voxel-driven gather
+//                     over the ray table (each voxel sums len * r over the bins
+//                     of its shadow), the partial sums of a CTA's view groups
+//                     added in shared memory in a fixed order, g^T g in FP64.
+//                     No atomics.
+//   k_forward_dual    p = A x_J and q = A g_J in one walk per ray, ||q||^2 in
+//                     FP64, the step length mu computed by the last CTA of each
+//                     slot (Alg. 1, Eq. 'step').
+//   k_epilogue        z_I^j = p + mu q, r -= z_new - z_old (the refresh of
+//                     Alg. 2-4 applied incrementally), x^_J += x_J + mu g_J.
+//   k_average         x_J = x^_J / count_J at the end of an epoch
+//                     (k_apply_pending first under epoch sync).
+// The kernels of the solver's batch sequence are launched with programmatic
+// stream serialization (see pdl_wait in device.cuh).
 #include <cuda_runtime.h>
-#include <stdio.h>
 
 #include <algorithm>
-#include <utility>
 #include <mutex>
+#include <utility>
 
 #include "device.cuh"
 #include "ops.h"
