@@ -141,8 +141,8 @@ int32_t csgd_project_block(const csgd_partition* part, const int32_t* row_blocks
 /* g[v] = (accumulate ? g[v] : 0) + sum_{i in I} A_iv r_i for every voxel v of
  * tile j (other voxels untouched); I = union of row_blocks.  r: full sinogram
  * (device); g: full volume (device).  The same Siddon lengths as
- * csgd_project_block, accumulated per tile in shared memory (no global
- * atomics) and reduced across a thread-block cluster. */
+ * csgd_project_block (the same plane crossings), gathered per voxel over the
+ * rays of its shadow (no atomics), with compensated accumulation over views. */
 int32_t csgd_backproject_block(const csgd_partition* part, const int32_t* row_blocks,
                                int32_t n_rb, int32_t j, const float* r, float* g,
                                int32_t accumulate, csgd_stream stream);
