@@ -785,11 +785,14 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
             const int kv = it.v0 + k / wu;
             const int64_t zi = zbase + (int64_t)kv * ew + ku;
             const int64_t ray = ray_index(G, it.view, ku, kv);
-            float zn = fmaf(mu, a.sb.q[ray], a.sb.p[ray]);
-            float zo = a.sb.z[zi];
+            // every load before any store: the arrays are distinct, so all four
+            // requests are in flight together
+            float* rd = a.sync_epoch ? a.sb.d : a.sb.r;
+            const float pv = __ldcg(a.sb.p + ray), qv = __ldcg(a.sb.q + ray);
+            const float zo = __ldcg(a.sb.z + zi), rv = __ldcg(rd + ray);
+            const float zn = fmaf(mu, qv, pv);
             a.sb.z[zi] = zn;
-            if (a.sync_epoch) a.sb.d[ray] += zn - zo;
-            else a.sb.r[ray] -= zn - zo;
+            rd[ray] = a.sync_epoch ? rv + (zn - zo) : rv - (zn - zo);
         }
     } else {
         const DevTile t = G.tiles[a.j];
