@@ -214,7 +214,11 @@ def run_reference(args, cfg, world, rank):
         "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": cfg["name"], "step": "one block step (Alg. 1) of the workload"},
+        "config": {"workload": cfg["name"], "block_steps_per_solve": int(cfg["steps"]),
+                   "n_rays": int(og.n_rays), "n_voxels": int(og.grid.size),
+                   "parallelism": "host cores (FP64 oracle)",
+                   "step": "one block step (Alg. 1) of the workload's schedule, a bounded "
+                           "sample of its solve"},
         "cpu_baseline": {"value": value, "unit": "updates/s", "cores": siddon.num_threads(),
                          "kind": "oracle",
                          "sample": "%d block steps of %s after %d warm-up steps"
