@@ -65,7 +65,6 @@ struct DevGeom {
     float pu, pv;          // bin pitch in voxel units (radians for the curved arc)
     float cu, cv;          // (nu-1)/2, (nv-1)/2
     float inv_pu, inv_pv;  // 1 / pu, 1 / pv
-    int32_t fast_arc;      // curved detector within |gamma| < 0.46 rad: series atan
     float h;               // voxel edge (world units): lengths are scaled by h
     const DevView* views;
     const DevVT* vt;       // [view][tile]

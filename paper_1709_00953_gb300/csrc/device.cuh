@@ -325,26 +325,6 @@ __device__ __forceinline__ void pdl_trigger() {
 }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// Reciprocal by the hardware approximation (rcp.approx: relative error about
-// 1e-7); used only where a result picks candidate bins under a margin.
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// atan x by its Taylor series to x^11: error below |x|^13 / 13 < 1e-5 rad on
-// |x| <= 0.5 (the alternating series' first dropped term).
-__device__ __forceinline__ float atan_series(float x) {
-    const float x2 = x * x;
-    float p = fmaf(x2, -1.0f / 11.0f, 1.0f / 9.0f);
-    p = fmaf(x2, p, -1.0f / 7.0f);
-    p = fmaf(x2, p, 1.0f / 5.0f);
-    p = fmaf(x2, p, -1.0f / 3.0f);
-    p = fmaf(x2, p, 1.0f);
-    return x * p;
-}
-
 // Compensated (Kahan) accumulator: the stand-alone projection's ray sums and
 // the backprojection's per-voxel sums over views.
 struct Kahan {

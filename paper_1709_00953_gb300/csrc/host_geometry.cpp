@@ -535,7 +535,6 @@ int partition_build(const Geometry* gp, const csgd_partition_desc* d, Partition*
     dg.cu = (float)cu;
     dg.cv = (float)cv;
     dg.inv_pu = (float)(1.0 / pu_v);
-    dg.fast_arc = (g.kind == CSGD_FAN_2D_CURVED && 0.5 * g.nu * pu_v + 2 * pu_v < 0.46) ? 1 : 0;
     dg.inv_pv = (float)(1.0 / pv_v);
     dg.h = (float)g.h;
     return CSGD_OK;

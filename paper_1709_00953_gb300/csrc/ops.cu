@@ -393,22 +393,22 @@ struct BPArgs {
 // case: a parallel ray's crossings are +-inf, which constrain nothing when q is
 // inside the slab and empty the interval when it is outside.
 
-// bins added on each side of a voxel's shadow window: covers the series atan
-// (below 0.011 bin at the finest pitch used), the approximate reciprocals
-// (relative error ~1e-7) and FP32 rounding
+// bins added on each side of a voxel's shadow window: covers the FP32 rounding
+// of the window's centre, gradient and half-width
 constexpr float kShadowMargin = 0.02f;
 constexpr int kViewBatch = 96;
 constexpr int kBPViewsPerPass = 2;  // 2D gather: views whose candidate loads are in flight together
 
-// Per-view data of a 2D backprojection CTA, staged in shared memory.  For voxel
-// (i0, i1) of the tile, r = P - S = (R0 + i0, R1 + i1); its depth along the
-// central ray is r . d_c and its lateral offset r . e_u with e_u = (d_c1, -d_c0)
-// (the 2D detector frame is d_c = -(cos t, sin t), e_u = (-sin t, cos t)).
+// Per-view data of a 2D backprojection CTA, staged in shared memory: the bin
+// coordinate of its 8 x 8 voxel patch, linearised about the patch centre Pc.
+// For a voxel at Pc + d the candidate window is [w + g . d - h, w + g . d + h],
+// where h covers the voxel's own shadow anywhere in the patch and the error of
+// the linearisation (see stage_view).
 struct alignas(16) ViewCtx2 {
-    float R0, R1, dc0, dc1;
-    float k;     // flat: sdd / pitch; parallel: the shadow's half-width + margin
-    int u0, u1;  // bins of the work item
-    int rbase;   // table position of bin 0 of the item
+    float w, g0, g1, h;  // bin coordinate of Pc minus 1/2, its gradient, half-width
+    int u0, u1;          // bins of the work item
+    int rbase;           // table position of bin 0 of the item
+    int pad;
 };
 
 // Per-view data of a 3D backprojection CTA: the detector coordinates of its
@@ -430,19 +430,63 @@ struct ViewCtxOf { using type = ViewCtx3; };
 template <>
 struct ViewCtxOf<2> { using type = ViewCtx2; };
 
-__device__ __forceinline__ void stage_view(const DevGeom& G, const DevTile& t, const WorkItem& it,
-                                           ViewCtx2* c, const float*) {
+// 2D detector coordinate of a point P: parallel beam w = (P . e_u) / pitch,
+// curved fan w = atan2(L, D) / pitch (the angle of r = P - S in the frame
+// (d_c, e_u)), flat fan w = k L / D with k = sdd / pitch, L = r . e_u, D = r . d_c
+// (e_u = (d_c1, -d_c0) in 2D).  Over the voxel centres of an 8 x 8 patch,
+// |P - Pc| <= R = sqrt(2) 3.5; with Hm a bound of the Hessian's norm there
+//   |w(P) - w(Pc) - g . (P - Pc)| <= Hm R^2 / 2,
+//   the first-order half-width 0.5 sum_k |dw/dP_k| of a voxel is at most its
+//   value at Pc plus 0.5 sqrt(2) Hm R,
+//   and a voxel's shadow is within its first-order half-width times
+//   (1 + 1.5 / depth) and within Hm / 4 (half diagonal^2 = 1/2) of it.
+// Hm: 0 (parallel: w is linear); 1 / (pitch rho_min^2) for the angle (the
+// Hessian of atan2 has norm 1 / |r|^2), rho_min = |r(Pc)| - R; k (2 / Dmin^2)
+// (1 + (|L| + R) / Dmin) for the flat detector, Dmin = D(Pc) - R.
+__device__ __forceinline__ void stage_view(const DevGeom& G, const DevTile&, const WorkItem& it,
+                                           ViewCtx2* c, const float* Pc) {
     const DevView& V = G.views[it.view];
-    const bool par = G.kind == PARALLEL_2D;
-    c->R0 = (t.T[0] - 0.5f * (float)t.n[0] + 0.5f) - (par ? 0.f : V.S[0]);
-    c->R1 = (t.T[1] - 0.5f * (float)t.n[1] + 0.5f) - (par ? 0.f : V.S[1]);
-    c->dc0 = V.dc[0];
-    c->dc1 = V.dc[1];
-    c->k = par ? fmaf(0.5f * (fabsf(V.dc[0]) + fabsf(V.dc[1])), G.inv_pu, kShadowMargin)
-               : V.sdd * G.inv_pu;
+    const float R = 4.9497475f;  // sqrt(2) * 3.5
+    const float wbase = fmaf(0.5f, (float)G.nu, -0.5f);
+    const float dc0 = V.dc[0], dc1 = V.dc[1], e0 = dc1, e1 = -dc0;
+    if (G.kind == PARALLEL_2D) {
+        c->w = fmaf(Pc[0] * e0 + Pc[1] * e1, G.inv_pu, wbase);
+        c->g0 = e0 * G.inv_pu;
+        c->g1 = e1 * G.inv_pu;
+        c->h = fmaf(0.5f * (fabsf(e0) + fabsf(e1)), G.inv_pu, kShadowMargin);
+    } else {
+        const float r0 = Pc[0] - V.S[0], r1 = Pc[1] - V.S[1];
+        const float D = r0 * dc0 + r1 * dc1;
+        const float L = r0 * e0 + r1 * e1;
+        const float Dmin = D - R;
+        if (Dmin > 1.0f) {
+            float Hm;
+            if (G.kind == FAN_2D_CURVED) {
+                const float rho2 = D * D + L * L;
+                const float rmin = sqrtf(rho2) - R;
+                c->w = fmaf(atan2f(L, D), G.inv_pu, wbase);
+                c->g0 = (D * e0 - L * dc0) / rho2 * G.inv_pu;
+                c->g1 = (D * e1 - L * dc1) / rho2 * G.inv_pu;
+                Hm = G.inv_pu / (rmin * rmin);
+            } else {
+                const float k = V.sdd * G.inv_pu, iD = 1.0f / D;
+                c->w = fmaf(k * L, iD, wbase);
+                c->g0 = k * (e0 * D - L * dc0) * iD * iD;
+                c->g1 = k * (e1 * D - L * dc1) * iD * iD;
+                Hm = k * 2.0f / (Dmin * Dmin) * (1.0f + (fabsf(L) + R) / Dmin);
+            }
+            const float h1 = 0.5f * (fabsf(c->g0) + fabsf(c->g1)) + 0.70710678f * Hm * R;
+            c->h = h1 * (1.0f + 1.5f / Dmin) + 0.25f * Hm + 0.5f * Hm * R * R + kShadowMargin;
+        } else {
+            // the patch reaches the source: every bin of the item is a candidate
+            c->w = c->g0 = c->g1 = 0.f;
+            c->h = 1e30f;
+        }
+    }
     c->u0 = it.u0;
     c->u1 = it.u1;
     c->rbase = (int)it.ray_off - it.u0;
+    c->pad = 0;
 }
 
 // Flat detector (cone beam, custom poses): w(P) = k L / D with D = r . d_c,
@@ -545,41 +589,13 @@ struct Cand2 {
     const RayRec* row;
 };
 
-__device__ __forceinline__ Cand2 view_cands(const DevGeom& G, const ViewCtx2& c, float xf, float yf,
+__device__ __forceinline__ Cand2 view_cands(const ViewCtx2& c, float dx, float dy,
                                             const RayRec* __restrict__ tab) {
-    const float r0 = c.R0 + xf, r1 = c.R1 + yf;
-    const float depth = fmaf(r0, c.dc0, r1 * c.dc1);
-    const float lat = fmaf(r0, c.dc1, -(r1 * c.dc0));
-    const float wbase = fmaf(0.5f, (float)G.nu, -0.5f);  // bin k covers [k, k+1) + 1/2 shift
-    float wu, hu;
-    if (G.kind == PARALLEL_2D) {
-        wu = fmaf(lat, G.inv_pu, wbase);
-        hu = c.k;
-    } else {
-        // The voxel's shadow is [w - h1, w + h1] to first order, h1 = 0.5 sum_k
-        // |dw/dP_k|; the second derivative of a perspective or angular map is at
-        // most ~2 |grad w| / depth, so over half a voxel diagonal (|delta|^2 <=
-        // 3/4) the second-order term is below 1.5 h1 / depth: h = h1 (1 + 1.5 /
-        // depth).  In 2D the two gradient terms are |r1| and |r0| scaled by
-        // 1 / (pitch |r|^2) (curved) or sdd / (pitch depth^2) (flat), since
-        // depth e_u - lat d_c is r turned by 90 degrees.
-        const float rd = rcp_approx(depth);
-        const float grow = fmaf(1.5f, rd, 1.0f);
-        const float l1 = fabsf(r0) + fabsf(r1);  // |d(r . e_u, r . d_c)|_1 terms of grad w
-        if (G.kind == FAN_2D_CURVED) {
-            float gam;
-            if (G.fast_arc) gam = atan_series(lat * rd);
-            else gam = atan2f(lat, depth);
-            wu = fmaf(gam, G.inv_pu, wbase);
-            hu = fmaf(0.5f * G.inv_pu * l1 * rcp_approx(fmaf(r0, r0, r1 * r1)), grow, kShadowMargin);
-        } else {
-            wu = fmaf(lat * rd, c.k, wbase);
-            hu = fmaf(0.5f * c.k * l1 * rd * rd, grow, kShadowMargin);
-        }
-    }
+    const float wu = fmaf(c.g1, dy, fmaf(c.g0, dx, c.w));
+    const float hu = c.h;
     Cand2 k;
-    k.ku0 = max(c.u0, __float2int_ru(wu - hu));
-    k.ku1 = min(c.u1 - 1, __float2int_rd(wu + hu));
+    k.ku0 = max(c.u0, __float2int_ru(fmaxf(wu - hu, -1e9f)));
+    k.ku1 = min(c.u1 - 1, __float2int_rd(fminf(wu + hu, 1e9f)));
     k.row = tab + c.rbase;
     // The first two candidates without branches (most voxels have one or two,
     // and lanes of a warp differ): both records are loaded from bins clamped
@@ -667,12 +683,13 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
     const int x2 = DIM == 3 ? (b12 / nb1) * 4 + lv / (P0 * P1) : 0;
     const bool valid = x0 < t.n[0] && x1 < t.n[1] && x2 < t.n[2];
     const int v = (x2 * t.n[1] + x1) * t.n[0] + x0;  // tile-local voxel index
-    // 3D: patch centre (tile-centred) and this voxel's offset from it
-    const float Pc[3] = {-0.5f * (float)t.n[0] + (float)(b0 * P0) + 2.0f + t.T[0],
-                         -0.5f * (float)t.n[1] + (float)((b12 % nb1) * P1) + 2.0f + t.T[1],
-                         -0.5f * (float)t.n[2] + (float)((b12 / nb1) * 4) + 2.0f + t.T[2]};
-    const float dP[3] = {(float)(lv % P0) - 1.5f, (float)((lv / P0) % P1) - 1.5f,
-                         (float)(lv / (P0 * P1)) - 1.5f};
+    // patch centre (grid-centred voxel units) and this voxel's offset from it
+    const float Pc[3] = {-0.5f * (float)t.n[0] + (float)(b0 * P0) + 0.5f * P0 + t.T[0],
+                         -0.5f * (float)t.n[1] + (float)((b12 % nb1) * P1) + 0.5f * P1 + t.T[1],
+                         DIM == 3 ? -0.5f * (float)t.n[2] + (float)((b12 / nb1) * 4) + 2.0f + t.T[2]
+                                  : 0.f};
+    const float dP[3] = {(float)(lv % P0) - 0.5f * (P0 - 1), (float)((lv / P0) % P1) - 0.5f * (P1 - 1),
+                         DIM == 3 ? (float)(lv / (P0 * P1)) - 1.5f : 0.f};
     // voxel box [lo, hi) in tile-centred coordinates, centre P
     float lo[3], hi[3], P[3];
     lo[0] = -0.5f * (float)t.n[0] + (float)x0;
@@ -702,11 +719,11 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
             for (; i + (V - 1) * C < nb; i += V * C) {
                 Cand2 k[V];
 #pragma unroll
-                for (int u = 0; u < V; ++u) k[u] = view_cands(G, vs[i + u * C], (float)x0, (float)x1, tab);
+                for (int u = 0; u < V; ++u) k[u] = view_cands(vs[i + u * C], dP[0], dP[1], tab);
 #pragma unroll
                 for (int u = 0; u < V; ++u) acc.add(cand_sum(k[u], lo, hi));
             }
-            for (; i < nb; i += C) acc.add(cand_sum(view_cands(G, vs[i], (float)x0, (float)x1, tab), lo, hi));
+            for (; i < nb; i += C) acc.add(cand_sum(view_cands(vs[i], dP[0], dP[1], tab), lo, hi));
         } else {
             for (int i = chunk; i < nb; i += C) acc.add(view_sum(G, vs[i], dP, lo, hi, tab));
         }
