@@ -790,7 +790,7 @@ static int64_t footprint(const csgd_partition* P, const csgd_solver_params* prm,
     int64_t ny = p.g->n_rays(), nx = p.g->n_voxels();
     *max_slots = groups_per_column(p, *prm);
     *max_rays = max_rays_per_step(p, std::max(1, prm->group_size));
-    *fwd_blocks = std::max<int64_t>(1, (*max_rays * 4 + 255) / 256);
+    *fwd_blocks = std::max<int64_t>(1, (*max_rays * 4 + kFwdThreads - 1) / kFwdThreads);
     *n_gg = bp_partials_per_slot(P);
     int64_t b = 0;
     b += 4 * (2 * nx);                           // x, xhat

@@ -31,7 +31,6 @@ namespace csgd {
 
 namespace {
 
-constexpr int kFwdThreads = 256;
 constexpr int kFwdBatch = 4;  // crossings per batch of gathers in the dual forward
 constexpr int kBPMaxThreads = kBPVox * kBPMaxChunks;
 constexpr int kEpiThreads = 256;

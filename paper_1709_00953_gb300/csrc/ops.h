@@ -22,6 +22,7 @@ struct InlineItems {
 // Backprojection launch: `blocks` CTAs per slot, each owning a patch of kBPVox
 // voxels of the tile (8 x 8 in 2D, 4 x 4 x 4 in 3D) with its views split among
 // C thread groups of kBPVox threads.
+constexpr int kFwdThreads = 128;  // threads of a dual-forward CTA (256 and 64 measured slower)
 constexpr int kBPVox = 64;
 constexpr int kBPMaxChunks = 8;  // view groups per CTA at most
 inline int bp_patch(int dim, int axis) { return dim == 2 ? (axis < 2 ? 8 : 1) : 4; }
