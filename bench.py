@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the library's launch-shape models instead of csgd_solver_autotune")
     a = ap.parse_args()
     if a.steps is None:
         a.steps = DEFAULT_STEPS.get(a.workload, 20)
@@ -286,8 +288,10 @@ def run_gpu(args, cfg, world, rank, local):
     rep = solver.solve(steps, None, report=True)
     nnz_per_solve = rep["nnz"]
     torch.cuda.synchronize()
-    # the solve as one CUDA graph (reset, every block step, epoch averages): the
-    # library's launch path for repeated solves
+    # launch shapes for this workload (csgd_solver_autotune, which resets the
+    # solver), then the solve as one CUDA graph (reset, every block step, epoch
+    # averages): the library's path for repeated solves
+    shapes = None if args.no_autotune else solver.autotune(min(steps, 16))
     graph = solver.graph(steps)
 
     def one_solve():
@@ -429,6 +433,8 @@ def run_gpu(args, cfg, world, rank, local):
                    "ms_per_epoch": ms / args.steps / max(1, int(rep["epochs"]))},
         "roofline": roof, "kernels": kernels, "gpu_launches": launches,
         "launch": "one CUDA graph per solve (reset, all block steps, epoch averages)",
+        "launch_shapes": ({"autotuned": True, "view_groups": shapes[0], "lanes_per_ray": shapes[1]}
+                          if shapes else {"autotuned": False}),
         "kernel_timing": "per-launch CUDA events in a second pass of the same %d solves launched "
                          "kernel by kernel (%.3f ms per solve that way)" % (args.steps, ms_instr / args.steps),
         "wall_s_timed": t_wall,
