@@ -50,8 +50,8 @@ DEFAULT_STEPS = {"fan2d_512": 250, "parallel2d_64": 250, "cone3d_256": 12, "batc
 # kernel sources they were taken from (hash of ops.cu, device.cuh, common.h);
 # "backproject" is the ray table plus the gather, the unit the bench times.
 NCU_TRAFFIC = {
-    ("fan2d_512_720x768_8x16_importance", "8411e977c42edde4"): {
-        "backproject": 2105344 + 390400, "forward_dual": 2535936},
+    ("fan2d_512_720x768_8x16_importance", "d1392583f64ff69f"): {
+        "backproject": 2105856 + 435712, "forward_dual": 2534912},
 }
 KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/csrc/device.cuh",
                   "paper_1709_00953_gb300/csrc/common.h")
