@@ -149,8 +149,6 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     const int sub = (int)(gid % L);
     const bool active = k < sd.n_rays;
     float pp = 0.f, qp = 0.f;
-    long long nz = 0;
-    int first_idx = -1, last_idx = -2;
     int ray = 0;
     if (active) {
         const RayRec* rp = a.sb.table + (int64_t)slot * a.sb.table_stride + k;
@@ -184,10 +182,6 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
                 for (int u = 0; u < kFwdBatch; ++u) {
                     px[u] = ln[u] * e[u].x;
                     py[u] = ln[u] * e[u].y;
-                    if (ln[u] > 0.f) {
-                        if (first_idx < 0) first_idx = id[u];
-                        last_idx = id[u];
-                    }
                 }
 #pragma unroll
                 for (int w = 1; w < kFwdBatch; w *= 2) {
@@ -200,16 +194,11 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
                 sx += px[0];
                 sy += py[0];
             };
-            if constexpr (DIM == 2) nz = walk2_batched<kFwdBatch>(q, inv, b, t0, t1, batch);
-            else nz = walk3_batched<kFwdBatch>(q, inv, b, t0, t1, batch);
+            if constexpr (DIM == 2) walk2_batched<kFwdBatch>(q, inv, b, t0, t1, batch);
+            else walk3_batched<kFwdBatch>(q, inv, b, t0, t1, batch);
             pp = sx;
             qp = sy;
         }
-    }
-    if (L > 1) {
-        // a voxel cut by the split between two lanes was counted by both
-        int prev_last = __shfl_up_sync(0xffffffffu, last_idx, 1);
-        if (sub > 0 && first_idx >= 0 && prev_last == first_idx) --nz;
     }
     float pv = G.h * lane_sum<L>(pp);
     float qv = G.h * lane_sum<L>(qp);
@@ -222,24 +211,14 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     // per-CTA partials (warps added in order in shared memory), then the last
     // CTA of the slot to finish adds the partials in a fixed order
     __shared__ double s_q[kFwdThreads / 32];
-    __shared__ long long s_n[kFwdThreads / 32];
     __shared__ unsigned s_last;
     const double wq = warp_sum(qq);
-    const long long wn = warp_sum_ll(nz);
-    if (lane == 0) {
-        s_q[threadIdx.x >> 5] = wq;
-        s_n[threadIdx.x >> 5] = wn;
-    }
+    if (lane == 0) s_q[threadIdx.x >> 5] = wq;
     __syncthreads();
     if (threadIdx.x == 0) {
         double cq = 0.0;
-        long long cn = 0;
-        for (int w = 0; w < kFwdThreads / 32; ++w) {
-            cq += s_q[w];
-            cn += s_n[w];
-        }
+        for (int w = 0; w < kFwdThreads / 32; ++w) cq += s_q[w];
         a.sb.qq_part[(int64_t)slot * a.sb.qq_stride + blockIdx.x] = cq;
-        if (cn) atomicAdd(a.sb.nnz_slot + slot, (unsigned long long)cn);
         __threadfence();
         const unsigned prev = atomicAdd(a.sb.counters + slot, 1u);
         s_last = prev == gridDim.x - 1;
@@ -259,6 +238,7 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     if (threadIdx.x == 0) {
         double mu = qs > 0.0 ? sd.beta * gs / qs : 0.0;
         a.sb.mu[slot] = mu;
+        // non-zeros of the step, counted by the backprojection
         unsigned long long nzs = atomicExch(a.sb.nnz_slot + slot, 0ull);
         atomicAdd(a.sb.nnz, nzs);
         if (sd.step >= 0 && sd.step < a.sb.hist_cap) {
@@ -380,6 +360,7 @@ struct BPArgs {
     int64_t slot_stride;
     double* gg_part;       // [slot][voxel blocks] or null
     int gg_stride;
+    unsigned long long* nnz_slot;  // [slot] non-zeros of the step, or null
 };
 
 // g_J = (A_I^J)^T r_I, voxel-driven: a thread owns one voxel of the tile and,
@@ -609,19 +590,27 @@ __device__ __forceinline__ Cand2 view_cands(const ViewCtx2& c, float dx, float d
     return k;
 }
 
-// sum over the candidate bins of len * r for one voxel (2D)
-__device__ __forceinline__ float cand_sum(const Cand2& k, const float lo[3], const float hi[3]) {
-    float s = fmaf(slab2(k.a0, lo, hi), k.rA, 0.f);
-    s = fmaf(slab2(k.a1, lo, hi), k.rB, s);
-    for (int ku = k.ku0 + 2; ku <= k.ku1; ++ku)
-        s = fmaf(slab2(rec_a(k.row + ku), lo, hi), k.row[ku].b[0], s);
+// sum over the candidate bins of len * r for one voxel (2D); nz counts the
+// candidates with a positive length (the non-zeros A_iv of the block)
+__device__ __forceinline__ float cand_sum(const Cand2& k, const float lo[3], const float hi[3],
+                                          int& nz) {
+    const float lA = slab2(k.a0, lo, hi), lB = slab2(k.a1, lo, hi);
+    nz += (lA > 0.f && k.ku0 <= k.ku1) + (lB > 0.f && k.ku0 < k.ku1);
+    float s = fmaf(lA, k.rA, 0.f);
+    s = fmaf(lB, k.rB, s);
+    for (int ku = k.ku0 + 2; ku <= k.ku1; ++ku) {
+        const float l = slab2(rec_a(k.row + ku), lo, hi);
+        nz += l > 0.f;
+        s = fmaf(l, k.row[ku].b[0], s);
+    }
     return s;
 }
 
-// sum over the view's candidate bins of len * r for one voxel (3D); d = P - Pc
+// sum over the view's candidate bins of len * r for one voxel (3D), d = P - Pc;
+// nz counts the candidates with a positive length
 __device__ __forceinline__ float view_sum(const DevGeom&, const ViewCtx3& c, const float d[3],
                                           const float lo[3], const float hi[3],
-                                          const RayRec* __restrict__ tab) {
+                                          const RayRec* __restrict__ tab, int& nz) {
     const float wu = fmaf(c.gu2, d[2], fmaf(c.gu1, d[1], fmaf(c.gu0, d[0], c.wu)));
     const float wv = fmaf(c.gv2, d[2], fmaf(c.gv1, d[1], fmaf(c.gv0, d[0], c.wv)));
     const int ku0 = max(c.u0, __float2int_ru(fmaxf(wu - c.hu, -1e9f)));
@@ -641,16 +630,22 @@ __device__ __forceinline__ float view_sum(const DevGeom&, const ViewCtx3& c, con
     const RayRec* p11 = base + vB * wdt + kB;
     const float4 a00 = rec_a(p00), b00 = rec_b(p00), a01 = rec_a(p01), b01 = rec_b(p01);
     const float4 a10 = rec_a(p10), b10 = rec_b(p10), a11 = rec_a(p11), b11 = rec_b(p11);
-    float s = fmaf(slab3(a00, b00, lo, hi), uA && wA ? b00.x : 0.f, 0.f);
-    s = fmaf(slab3(a01, b01, lo, hi), uB && wA ? b01.x : 0.f, s);
-    s = fmaf(slab3(a10, b10, lo, hi), uA && wB ? b10.x : 0.f, s);
-    s = fmaf(slab3(a11, b11, lo, hi), uB && wB ? b11.x : 0.f, s);
+    const float l00 = slab3(a00, b00, lo, hi), l01 = slab3(a01, b01, lo, hi);
+    const float l10 = slab3(a10, b10, lo, hi), l11 = slab3(a11, b11, lo, hi);
+    nz += (l00 > 0.f && uA && wA) + (l01 > 0.f && uB && wA) + (l10 > 0.f && uA && wB) +
+          (l11 > 0.f && uB && wB);
+    float s = fmaf(l00, uA && wA ? b00.x : 0.f, 0.f);
+    s = fmaf(l01, uB && wA ? b01.x : 0.f, s);
+    s = fmaf(l10, uA && wB ? b10.x : 0.f, s);
+    s = fmaf(l11, uB && wB ? b11.x : 0.f, s);
     for (int kv = kv0; kv <= kv1; ++kv) {
         const RayRec* row = base + kv * wdt;
         for (int ku = (kv < kv0 + 2 ? ku0 + 2 : ku0); ku <= ku1; ++ku) {
             const RayRec* rp = row + ku;
             const float4 b = rec_b(rp);
-            s = fmaf(slab3(rec_a(rp), b, lo, hi), b.x, s);
+            const float l = slab3(rec_a(rp), b, lo, hi);
+            nz += l > 0.f;
+            s = fmaf(l, b.x, s);
         }
     }
     return s;
@@ -702,6 +697,7 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
     const RayRec* __restrict__ tab = a.table + (int64_t)slot * a.table_stride;
     const int n_items = sd.w1 - sd.w0;
     Kahan acc;
+    int nz = 0;  // candidates of this voxel with a positive length
     for (int base = 0; base < n_items; base += kViewBatch) {
         const int nb = min(kViewBatch, n_items - base);
         __syncthreads();
@@ -720,11 +716,12 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
 #pragma unroll
                 for (int u = 0; u < V; ++u) k[u] = view_cands(vs[i + u * C], dP[0], dP[1], tab);
 #pragma unroll
-                for (int u = 0; u < V; ++u) acc.add(cand_sum(k[u], lo, hi));
+                for (int u = 0; u < V; ++u) acc.add(cand_sum(k[u], lo, hi, nz));
             }
-            for (; i < nb; i += C) acc.add(cand_sum(view_cands(vs[i], dP[0], dP[1], tab), lo, hi));
+            for (; i < nb; i += C)
+                acc.add(cand_sum(view_cands(vs[i], dP[0], dP[1], tab), lo, hi, nz));
         } else {
-            for (int i = chunk; i < nb; i += C) acc.add(view_sum(G, vs[i], dP, lo, hi, tab));
+            for (int i = chunk; i < nb; i += C) acc.add(view_sum(G, vs[i], dP, lo, hi, tab, nz));
         }
     }
     if (n_items <= 0) pdl_wait();
@@ -747,6 +744,19 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
     if (a.gg_part) {
         double bg = block_sum(gg, sh);
         if (threadIdx.x == 0) a.gg_part[(int64_t)slot * a.gg_stride + blockIdx.x] = bg;
+    }
+    if (a.nnz_slot) {
+        // nnz(A_I^J) of the step: each (voxel, ray) pair is clipped by exactly
+        // one thread, with the lengths the forward walk uses
+        __shared__ long long s_nz[kBPMaxThreads / 32];
+        const long long wn = warp_sum_ll((long long)nz);
+        if ((threadIdx.x & 31) == 0) s_nz[threadIdx.x >> 5] = wn;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long cn = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) cn += s_nz[w];
+            if (cn) atomicAdd(a.nnz_slot + slot, (unsigned long long)cn);
+        }
     }
 }
 
@@ -1065,6 +1075,7 @@ cudaError_t launch_backproject_inline(const DevGeom& G, const DevTile& tile,
     a.slot_stride = 0;
     a.gg_part = nullptr;
     a.gg_stride = 0;
+    a.nnz_slot = nullptr;
     e = launch_bp_common(G, plan, 1, s, a, &it, nullptr, nullptr);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -1133,6 +1144,7 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     a.slot_stride = sb.g_stride;
     a.gg_part = sb.gg_part;
     a.gg_stride = sb.gg_stride;
+    a.nnz_slot = sb.nnz_slot;
     e = launch_bp_common(G, plan, b.nslots, s, a, nullptr, items, steps);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
