@@ -71,9 +71,9 @@ struct DevGeom {
     const DevTile* tiles;
 };
 
-// Per-ray table of one launch (ray set-up done once, read by the
-// backprojection): tile-centred point q, reciprocal direction 1/d (infinite
-// where d = 0) and the residual r of the ray.
+// Per-ray table of one launch (ray set-up done once, read by the backprojection
+// and the dual forward): tile-centred point q, reciprocal direction 1/d
+// (infinite where d = 0) and the residual r of the ray.
 struct alignas(16) RayRec {
     float a[4];  // q[0], q[1], inv[0], inv[1]
     float b[4];  // r, q[2], inv[2], index of the ray in the sinogram (int bits, < 2^31)
