@@ -67,13 +67,22 @@ int ensure_device(csgd_partition* P) {
     size_t bv = sizeof(DevView) * p.views_h.size();
     size_t bt = sizeof(DevVT) * p.vt_h.size();
     size_t bti = sizeof(DevTile) * p.tiles_h.size();
-    CSGD_CUDA(cudaMalloc(&p.d_views, bv), "cudaMalloc(views)");
-    CSGD_CUDA(cudaMalloc(&p.d_vt, bt), "cudaMalloc(view-tile table)");
-    CSGD_CUDA(cudaMalloc(&p.d_tiles, bti), "cudaMalloc(tiles)");
-    CSGD_CUDA(cudaMemcpy(p.d_views, p.views_h.data(), bv, cudaMemcpyHostToDevice), "upload views");
-    CSGD_CUDA(cudaMemcpy(p.d_vt, p.vt_h.data(), bt, cudaMemcpyHostToDevice), "upload table");
-    CSGD_CUDA(cudaMemcpy(p.d_tiles, p.tiles_h.data(), bti, cudaMemcpyHostToDevice),
-              "upload tiles");
+    cudaError_t e = cudaMalloc(&p.d_views, bv);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_vt, bt);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_tiles, bti);
+    if (e == cudaSuccess) e = cudaMemcpy(p.d_views, p.views_h.data(), bv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p.d_vt, p.vt_h.data(), bt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p.d_tiles, p.tiles_h.data(), bti, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        // leave the partition as it was: nothing on the device
+        cudaFree(p.d_views);
+        cudaFree(p.d_vt);
+        cudaFree(p.d_tiles);
+        p.d_views = nullptr;
+        p.d_vt = nullptr;
+        p.d_tiles = nullptr;
+        return cuda_fail(e, "upload partition tables");
+    }
     p.dg.views = p.d_views;
     p.dg.vt = p.d_vt;
     p.dg.tiles = p.d_tiles;
