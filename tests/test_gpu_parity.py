@@ -279,3 +279,48 @@ def test_checkpoint_resume_is_exact(csgd, name):
         b.set_state(bad)
     with pytest.raises(RuntimeError):
         b.set_state(st[:100])
+
+
+@pytest.mark.parametrize("name,override,steps", [
+    ("fan_curved_ragged", dict(sampling=0), 40),                                  # Alg. 2 order
+    ("fan_curved_ragged", dict(sampling=1, gamma=0.5, alpha=0.5, group_size=2), 40),
+    ("fan_flat_ragged", dict(sampling=2, gamma=0.5, b=2.0), 40),                 # tiles skipped per epoch
+    ("cone_ragged", dict(sampling=3, sync=1, group_size=2, gamma=0.75, theta_step=0.5), 30),
+])
+def test_solver_variants_parity(csgd, name, override, steps):
+    """Schedules the paper allows beyond the default: sequential order, uniform
+    groups, gamma < 1 (some column blocks unvisited in an epoch, so their count
+    is 0 and x_J keeps its value), mixed sampling with epoch sync."""
+    cfg = dict(CASES[name])
+    cfg["solver"] = dict(cfg["solver"], **override)
+    x_gpu, x_ref, hist, o, rep, y = _solver_pair(csgd, cfg, steps)
+    assert len(hist) == steps == len(o.log)
+    np.testing.assert_allclose([h["beta"] for h in hist], [l["beta"] for l in o.log], rtol=1e-12)
+    np.testing.assert_allclose([h["mu"] for h in hist], [l["mu"] for l in o.log], rtol=REL,
+                               atol=1e-12)
+    assert float(np.sqrt(np.mean((x_gpu - x_ref) ** 2))) <= 1e-4
+
+
+def test_single_block_is_steepest_descent(csgd):
+    """m = n = 1 (one row block, one tile): every step is a full steepest-descent
+    step with exact line search, so ||y - A x|| does not increase; the GPU run
+    matches the oracle step for step."""
+    cfg = dict(CASES["parallel64"])
+    cfg["part"] = dict(tiles=(1, 1), view_blocks=1, det_blocks=(1, 1))
+    cfg["solver"] = dict(cfg["solver"], sampling=0, alpha=1.0, gamma=1.0, b=1.0)
+    y, _ = D.make_data(cfg)
+    p, op = _pair(csgd, cfg)
+    yt = torch.tensor(y, device="cuda")
+    s = csgd.Solver(p, cfg["solver"], yt)
+    o = OracleSolver(op, cfg["solver"], y.astype(np.float64))
+    norms = []
+    x = torch.zeros(p.n_voxels, dtype=torch.float32, device="cuda")
+    for k in range(12):
+        rep = s.solve(1, x, residual=True)
+        norms.append(rep["residual_norm"])
+    xo = o.run(12)
+    mu_g = np.array([h["mu"] for h in s.history()])
+    mu_o = np.array([l["mu"] for l in o.log])
+    np.testing.assert_allclose(mu_g, mu_o, rtol=REL)
+    assert all(b <= a * (1 + 1e-6) for a, b in zip(norms, norms[1:]))
+    assert float(np.sqrt(np.mean((x.cpu().numpy() - xo) ** 2))) <= 1e-4
