@@ -549,6 +549,12 @@ def run_serve(args, world, rank, local):
     # warm-up: a few jobs served back to back
     warm = [serve.Job(c, y, 0.0, c["name"]) for c, y in list(zip(cfgs, ys))[:max(1, args.warmup)]]
     serve.Server(budget).run(warm)
+    # capacity: every job queued at t = 0 (the server's throughput limit)
+    sat = [serve.Job(c, y, 0.0, c["name"]) for c, y in zip(cfgs, ys)]
+    t0 = time.perf_counter()
+    serve.Server(budget, max_running=16).run(sat)
+    cap = serve.summary(sat, time.perf_counter() - t0)
+    # latency at the configured Poisson arrival rate
     arrivals = serve.poisson_arrivals(len(cfgs), args.rate, seed=1709 + 4)
     jobs = [serve.Job(c, y, float(a), c["name"]) for c, y, a in zip(cfgs, ys, arrivals)]
     srv = serve.Server(budget, max_running=16)
@@ -570,6 +576,10 @@ def run_serve(args, world, rank, local):
         "latency": {"p50_s": s["p50_latency_s"], "p99_s": s["p99_latency_s"],
                     "mean_s": s["mean_latency_s"]},
         "max_concurrency": srv.max_concurrency, "wall_s": wall,
+        "arrival_window_s": float(arrivals[-1]),
+        "capacity": {"solves_per_s": cap["solves_per_s"], "p50_latency_s": cap["p50_latency_s"],
+                     "p99_latency_s": cap["p99_latency_s"],
+                     "note": "all jobs queued at t = 0: the throughput limit of the server"},
         "quality": "each job runs its fixed step count; served results equal solo solves bit "
                    "for bit and match the FP64 oracle's solution of the same job within RMSE "
                    "1e-3 (GPU tests)",
