@@ -809,7 +809,7 @@ static int64_t footprint(const csgd_partition* P, const csgd_solver_params* prm,
     b += 4 * std::max<int64_t>(1, p.z_floats);   // z store
     b += 8 * (int64_t)(*max_slots) * p.max_tile_voxels;  // (x, g) pairs per slot
     b += (int64_t)sizeof(RayRec) * (*max_slots) * (*max_rays);  // ray tables
-    b += 8 * (int64_t)(*max_slots) * (*n_gg + *fwd_blocks + 1) + 4 * (*max_slots);
+    b += 4 * (int64_t)(*max_slots) * (*n_gg + *fwd_blocks) + 20 * (int64_t)(*max_slots);  // partials, mu, counters, nnz
     return b;
 }
 
@@ -872,10 +872,10 @@ int32_t csgd_solver_create(const csgd_partition* Pc, const csgd_solver_params* p
     ALLOC(b.p, sizeof(float) * S->n_rays, "cudaMalloc(p)");
     ALLOC(b.q, sizeof(float) * S->n_rays, "cudaMalloc(q)");
     ALLOC(b.g, 2 * sizeof(float) * b.max_slots * b.g_stride, "cudaMalloc(x, g pairs)");
-    ALLOC(b.gg_part, sizeof(double) * b.max_slots * ng, "cudaMalloc(gg partials)");
+    ALLOC(b.gg_part, sizeof(float) * b.max_slots * ng, "cudaMalloc(gg partials)");
     ALLOC(b.table, sizeof(RayRec) * b.max_slots * b.table_stride, "cudaMalloc(ray tables)");
     b.qq_stride = b.max_fwd_blocks;  // one q^T q partial per forward CTA
-    ALLOC(b.qq_part, sizeof(double) * b.max_slots * b.qq_stride, "cudaMalloc(qq partials)");
+    ALLOC(b.qq_part, sizeof(float) * b.max_slots * b.qq_stride, "cudaMalloc(qq partials)");
     ALLOC(b.counters, sizeof(unsigned) * b.max_slots, "cudaMalloc(counters)");
     ALLOC(b.mu, sizeof(double) * b.max_slots, "cudaMalloc(mu)");
     ALLOC(b.nnz, sizeof(unsigned long long), "cudaMalloc(nnz)");

@@ -343,7 +343,26 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
+// Running sum of FP32 terms kept exactly as an unevaluated pair s + c
+// (Knuth's TwoSum gives each addition's rounding error exactly; the errors are
+// added into c, whose own rounding is second order, O(n u^2)).  Used where
+// many FP32 partials are added: FP32 ALU work instead of FP64.
+struct TwoSumF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float t = s + v;
+        const float bp = t - s;
+        c += (s - (t - bp)) + (v - bp);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// FP32 butterfly sum of non-negative terms (squares): a tree of depth 5, so the
+// result is within 5 u of the exact sum (u = 2^-24).  GB300's FP64 pipe runs
+// at about 1/64 of the FP32 rate, so per-thread terms are reduced in FP32 up to
+// the CTA and only CTA partials are added in FP64.
+__device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;

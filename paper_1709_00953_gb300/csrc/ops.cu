@@ -202,22 +202,24 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     }
     float pv = G.h * lane_sum<L>(pp);
     float qv = G.h * lane_sum<L>(qp);
-    double qq = 0.0;
+    float qq = 0.f;
     if (active && sub == 0) {
         a.sb.p[ray] = pv;
         a.sb.q[ray] = qv;
-        qq = (double)qv * (double)qv;
+        qq = qv * qv;
     }
-    // per-CTA partials (warps added in order in shared memory), then the last
-    // CTA of the slot to finish adds the partials in a fixed order
+    // per-CTA partials in FP32 (the squares, a warp tree, then the warps in
+    // order: within 9 u of the CTA's exact sum of squares), then the last CTA
+    // of the slot to finish adds the partials in FP64 in a fixed order
     __shared__ double s_q[kFwdThreads / 32];
+    __shared__ float s_qf[kFwdThreads / 32];
     __shared__ unsigned s_last;
-    const double wq = warp_sum(qq);
-    if (lane == 0) s_q[threadIdx.x >> 5] = wq;
+    const float wq = warp_sum_f(qq);
+    if (lane == 0) s_qf[threadIdx.x >> 5] = wq;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double cq = 0.0;
-        for (int w = 0; w < kFwdThreads / 32; ++w) cq += s_q[w];
+        float cq = 0.f;
+        for (int w = 0; w < kFwdThreads / 32; ++w) cq += s_qf[w];
         a.sb.qq_part[(int64_t)slot * a.sb.qq_stride + blockIdx.x] = cq;
         __threadfence();
         const unsigned prev = atomicAdd(a.sb.counters + slot, 1u);
@@ -226,15 +228,15 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // thread t adds partials t, t + blockDim.x, ... in order; then a fixed tree
-    double qs = 0.0;
+    // thread t adds partials t, t + blockDim.x, ... in order, error-free in
+    // FP32 pairs; then a fixed FP64 tree over the threads
+    TwoSumF tq, tg;
     for (int w = threadIdx.x; w < (int)gridDim.x; w += blockDim.x)
-        qs += __ldcg(a.sb.qq_part + (int64_t)slot * a.sb.qq_stride + w);
-    qs = block_sum(qs, s_q);
-    double gs = 0.0;
+        tq.add(__ldcg(a.sb.qq_part + (int64_t)slot * a.sb.qq_stride + w));
     for (int w = threadIdx.x; w < a.n_gg; w += blockDim.x)
-        gs += __ldcg(a.sb.gg_part + (int64_t)slot * a.sb.gg_stride + w);
-    gs = block_sum(gs, s_q);
+        tg.add(__ldcg(a.sb.gg_part + (int64_t)slot * a.sb.gg_stride + w));
+    const double qs = block_sum(tq.value(), s_q);
+    const double gs = block_sum(tg.value(), s_q);
     if (threadIdx.x == 0) {
         double mu = qs > 0.0 ? sd.beta * gs / qs : 0.0;
         a.sb.mu[slot] = mu;
@@ -358,7 +360,7 @@ struct BPArgs {
     int mode;
     int accumulate;
     int64_t slot_stride;
-    double* gg_part;       // [slot][voxel blocks] or null
+    float* gg_part;        // [slot][voxel blocks] or null
     int gg_stride;
     unsigned long long* nnz_slot;  // [slot] non-zeros of the step, or null
 };
@@ -660,7 +662,6 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
                                                  const StepDesc& sd, int slot) {
     using Ctx = typename ViewCtxOf<DIM>::type;
     __shared__ float part[kBPMaxThreads];
-    __shared__ double sh[kBPMaxThreads / 32];
     __shared__ Ctx vs[kViewBatch];
     const DevGeom& G = a.G;
     const int C = (int)blockDim.x / kBPVox;
@@ -727,7 +728,7 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
     if (n_items <= 0) pdl_wait();
     part[threadIdx.x] = acc.s - acc.c;
     __syncthreads();
-    double gg = 0.0;
+    float gg = 0.f;
     if (chunk == 0 && valid) {
         float s = 0.f;
         for (int c = 0; c < C; ++c) s += part[c * kBPVox + lv];
@@ -739,23 +740,35 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
             int64_t gi = ((int64_t)(t.lo[2] + x2) * G.ny + (t.lo[1] + x1)) * G.nx + t.lo[0] + x0;
             a.gout[gi] = a.accumulate ? a.gout[gi] + s : s;
         }
-        gg = (double)s * (double)s;
+        gg = s * s;
     }
+    // The CTA's g^T g partial in FP32 (a warp tree, then the warps in order:
+    // within 13 u of its exact value); and nnz(A_I^J) of the
+    // step: each (voxel, ray) pair is clipped by exactly one thread, with the
+    // lengths the forward walk uses.
+    __shared__ float s_gg[kBPMaxThreads / 32];
+    __shared__ unsigned s_nz[kBPMaxThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (a.gg_part) {
-        double bg = block_sum(gg, sh);
-        if (threadIdx.x == 0) a.gg_part[(int64_t)slot * a.gg_stride + blockIdx.x] = bg;
+        const float wg = warp_sum_f(gg);
+        if (lane == 0) s_gg[w] = wg;
     }
     if (a.nnz_slot) {
-        // nnz(A_I^J) of the step: each (voxel, ray) pair is clipped by exactly
-        // one thread, with the lengths the forward walk uses
-        __shared__ long long s_nz[kBPMaxThreads / 32];
-        const long long wn = warp_sum_ll((long long)nz);
-        if ((threadIdx.x & 31) == 0) s_nz[threadIdx.x >> 5] = wn;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            long long cn = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) cn += s_nz[w];
-            if (cn) atomicAdd(a.nnz_slot + slot, (unsigned long long)cn);
+        const unsigned wn = __reduce_add_sync(0xffffffffu, (unsigned)nz);
+        if (lane == 0) s_nz[w] = wn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        if (a.gg_part) {
+            float cg = 0.f;
+            for (int k = 0; k < nw; ++k) cg += s_gg[k];
+            a.gg_part[(int64_t)slot * a.gg_stride + blockIdx.x] = cg;
+        }
+        if (a.nnz_slot) {
+            unsigned long long cn = 0;
+            for (int k = 0; k < nw; ++k) cn += s_nz[k];
+            if (cn) atomicAdd(a.nnz_slot + slot, cn);
         }
     }
 }
@@ -792,6 +805,8 @@ struct EpiArgs {
 
 // CTAs 0 .. n_items-1 (x) update z and r on one work item's rays each; the
 // remaining CTAs add the batch's candidates into x^ of the tile.
+constexpr int kEpiMu = 32;
+
 __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
     pdl_trigger();
     const DevGeom& G = a.G;
@@ -829,10 +844,18 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
         const int64_t nthreads = (int64_t)(gridDim.x - a.n_items) * gridDim.y * blockDim.x;
         int64_t v0 = ((int64_t)(blockIdx.x - a.n_items) * gridDim.y + blockIdx.y) * blockDim.x +
                      threadIdx.x;
+        // the step lengths of the first kEpiMu slots converted once per CTA,
+        // not once per voxel
+        __shared__ float s_mu[kEpiMu];
+        const int nm = min(a.nslots, kEpiMu);
+        if ((int)threadIdx.x < nm) s_mu[threadIdx.x] = (float)a.sb.mu[threadIdx.x];
+        __syncthreads();
         for (int64_t v = v0; v < nv; v += nthreads) {
             float xv = x[v];
             float s = xh[v];
-            for (int sl = 0; sl < a.nslots; ++sl)
+            for (int sl = 0; sl < nm; ++sl)
+                s += fmaf(s_mu[sl], a.sb.g[2 * ((int64_t)sl * a.sb.g_stride + v) + 1], xv);
+            for (int sl = nm; sl < a.nslots; ++sl)
                 s += fmaf((float)a.sb.mu[sl], a.sb.g[2 * ((int64_t)sl * a.sb.g_stride + v) + 1], xv);
             xh[v] = s;
         }

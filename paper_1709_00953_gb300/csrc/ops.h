@@ -72,11 +72,11 @@ struct SolverBuffers {
     float* p;        // A x_J per ray
     float* q;        // A g_J per ray
     float* g;        // (x_J, g_J) pairs per slot, tile-local [slot][g_stride][2]
-    double* gg_part; // [slot][gg_stride]: g^T g per backprojection CTA
+    float* gg_part;  // [slot][gg_stride]: g^T g per backprojection CTA (FP32)
     int gg_stride;
     RayRec* table;   // [slot][table_stride]: ray table of the batch
     int64_t table_stride;
-    double* qq_part; // [slot][qq_stride]: q^T q per forward warp
+    float* qq_part;  // [slot][qq_stride]: q^T q per forward CTA (FP32)
     int qq_stride;
     unsigned int* counters;  // [slot]
     double* mu;      // [slot]

@@ -24,9 +24,9 @@ def mods():
     return csgd, serve
 
 
-def _jobs(serve, n=8):
+def _jobs(serve, n=8, rate_per_s=200.0):
     cfgs = C.serving_jobs(n_jobs=n, seed=77, small=True)
-    arrivals = serve.poisson_arrivals(n, rate_per_s=200.0, seed=5)
+    arrivals = serve.poisson_arrivals(n, rate_per_s=rate_per_s, seed=5)
     return [serve.Job(c, D.make_data(c)[0], float(a), c["name"]) for c, a in zip(cfgs, arrivals)]
 
 
@@ -42,7 +42,9 @@ def _solo(csgd, job):
 
 def test_served_results_equal_solo_results(mods):
     csgd, serve = mods
-    jobs = _jobs(serve)
+    # arrivals ~10 us apart: every small job takes longer than that, so jobs
+    # overlap whatever the speed of the kernels
+    jobs = _jobs(serve, rate_per_s=1e5)
     srv = serve.Server(hbm_budget_bytes=8 << 30, max_running=8)
     srv.run(jobs)
     assert srv.max_concurrency >= 2  # jobs did overlap
