@@ -132,6 +132,9 @@ __global__ void __launch_bounds__(kFwdThreads) k_project_inline(
 // up once for the backprojection), split over L lanes by parameter range.  Each
 // CTA writes its partial sums; the last CTA of the slot to finish adds them in a
 // fixed order and computes mu = beta g^T g / q^T q (no grid barrier).
+// (2^-12)^2: the smallest squared gain ||A g||^2 / (h^2 ||g||^2) of a step
+constexpr double kMinGain2 = 5.9604644775390625e-08;
+
 template <int DIM, int L>
 __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     pdl_trigger();
@@ -238,7 +241,11 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     const double qs = block_sum(tq.value(), s_q);
     const double gs = block_sum(tg.value(), s_q);
     if (threadIdx.x == 0) {
-        double mu = qs > 0.0 ? sd.beta * gs / qs : 0.0;
+        // the exact line search; skipped (mu = 0) when ||A g|| < 2^-12 h ||g||:
+        // support that small is rounding noise (a line through a tile corner),
+        // on which gs / qs ~ 1 / length^2 would throw x_J off
+        const double floor2 = kMinGain2 * (double)G.h * (double)G.h * gs;
+        double mu = qs > floor2 ? sd.beta * gs / qs : 0.0;
         a.sb.mu[slot] = mu;
         // non-zeros of the step, counted by the backprojection
         unsigned long long nzs = atomicExch(a.sb.nnz_slot + slot, 0ull);

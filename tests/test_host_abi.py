@@ -132,3 +132,23 @@ def test_footprint_grows_with_problem(lib):
     assert 0 < fa < fb
     # at least x, xhat, y, r, p, q and the z store
     assert fb >= 4 * (2 * pb.n_voxels + 4 * pb.n_rays + pb.z_floats)
+
+
+def test_sec3_study_step_counts(lib):
+    """The Sec. III re-runs read each epoch's group steps from the library's
+    schedule; the counts equal those of the oracle's draw (same geometry, seed)."""
+    from paper_1709_00953_gb300 import experiments as X
+    cfg = dict(geom=X.geometry_spec(),
+               part=dict(tiles=(2, 2), view_blocks=X.N_VIEWS, det_blocks=(2, 1)))
+    p, op = _pair(cfg)
+    prm = dict(sampling=2, alpha=0.5, gamma=0.75, b=25.0, group_size=5, seed=X.SCHEDULE_SEED,
+               theta_step=1.0 / 40.0)
+    flat = lib.schedule_generate(p, prm, 3)
+    rng = OS.SplitMix64(prm["seed"])
+    P = OP.probability_table(op)
+    vb = [op.row_block_parts(i)[0] for i in range(op.n_row_blocks)]
+    eps = [OS.epoch_schedule(rng, P, prm, e, vb) for e in range(3)]
+    assert flat == OS.flatten(eps)
+    counts = X.groups_per_epoch(flat, 3)
+    assert counts == [sum(len(g) for _, g in ep) for ep in eps]
+    assert all(c > 0 for c in counts)

@@ -122,3 +122,22 @@ def test_metrics_closed_forms():
     xt = np.array([3.0, 4.0])
     assert metrics.snr_db(xt, 0.9 * xt) == pytest.approx(20.0)
     assert metrics.rmse([1, 2, 3], [1, 2, 5]) == pytest.approx(np.sqrt(4 / 3))
+
+
+def test_step_length_one_entry_block_and_rounding_support():
+    """Eq. 'step' on a one-entry block A = [l]: g = l r and q = A g = l^2 r, so
+    mu = beta / l^2, and with beta = 1 the step solves the row exactly.  Support
+    below the gain floor 2^-12 h (rounding noise, e.g. a line through a tile
+    corner) takes no step."""
+    from oracle.solver import MIN_GAIN, step_length
+    h, r, beta = 0.5, 3.0, 0.7
+    assert MIN_GAIN == 2.0 ** -12
+    for ln in (0.8 * h, 0.01 * h, 1e-3 * h):
+        g = ln * r
+        q = ln * g
+        assert step_length(beta, g * g, q * q, h) == pytest.approx(beta / ln ** 2, rel=1e-14)
+        assert r - step_length(1.0, g * g, q * q, h) * q == pytest.approx(0.0, abs=1e-12 * r)
+    for ln in (1e-5 * h, 1e-9 * h, 0.0):
+        g = ln * r
+        q = ln * g
+        assert step_length(beta, g * g, q * q, h) == 0.0
