@@ -647,14 +647,16 @@ __device__ __forceinline__ float view_sum(const DevGeom&, const ViewCtx3& c, con
     s = fmaf(l01, uB && wA ? b01.x : 0.f, s);
     s = fmaf(l10, uA && wB ? b10.x : 0.f, s);
     s = fmaf(l11, uB && wB ? b11.x : 0.f, s);
-    for (int kv = kv0; kv <= kv1; ++kv) {
-        const RayRec* row = base + kv * wdt;
-        for (int ku = (kv < kv0 + 2 ? ku0 + 2 : ku0); ku <= ku1; ++ku) {
-            const RayRec* rp = row + ku;
-            const float4 b = rec_b(rp);
-            const float l = slab3(rec_a(rp), b, lo, hi);
-            nz += l > 0.f;
-            s = fmaf(l, b.x, s);
+    if (ku1 - ku0 >= 2 || kv1 - kv0 >= 2) {  // candidates beyond the 2 x 2 block
+        for (int kv = kv0; kv <= kv1; ++kv) {
+            const RayRec* row = base + kv * wdt;
+            for (int ku = (kv < kv0 + 2 ? ku0 + 2 : ku0); ku <= ku1; ++ku) {
+                const RayRec* rp = row + ku;
+                const float4 b = rec_b(rp);
+                const float l = slab3(rec_a(rp), b, lo, hi);
+                nz += l > 0.f;
+                s = fmaf(l, b.x, s);
+            }
         }
     }
     return s;
