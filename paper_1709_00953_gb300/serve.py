@@ -87,22 +87,34 @@ class Server:
         running: list[_Running] = []
         free_streams = list(self.streams)
         used = 0
+        # Finished jobs' device objects are released in batches, not one by
+        # one: freeing device memory waits for the whole device, which would
+        # stall the loop behind every running job.  Their bytes count against
+        # the budget until they are released.
+        retired: list[_Running] = []
+        retired_bytes = 0
         t0 = time.perf_counter()
         while waiting or running:
             now = time.perf_counter() - t0
-            # completions first: they free memory and streams
+            # completions first: they free streams (and, once released, memory)
             for r in list(running):
                 if r.finished():
                     r.job.done = time.perf_counter() - t0
                     r.job.latency = r.job.done - r.job.arrival
                     r.job.x = r.x_host.numpy().copy()
-                    used -= r.job.footprint
+                    retired_bytes += r.job.footprint
                     free_streams.append(r.stream)
                     running.remove(r)
-                    del r
+                    retired.append(r)
             # admissions in arrival order while the head job fits
-            while (waiting and waiting[0].arrival <= now and free_streams and
-                   used + waiting[0].footprint <= self.budget):
+            while waiting and waiting[0].arrival <= now and free_streams:
+                if used + waiting[0].footprint > self.budget:
+                    if not retired:
+                        break
+                    retired.clear()  # releases their device memory
+                    used -= retired_bytes
+                    retired_bytes = 0
+                    continue
                 job = waiting.pop(0)
                 job.admitted = time.perf_counter() - t0
                 used += job.footprint
@@ -111,6 +123,7 @@ class Server:
                 self.max_used = max(self.max_used, used)
             if waiting or running:
                 time.sleep(poll_s)
+        retired.clear()
         return jobs
 
 
