@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library's launch-shape models instead of csgd_solver_autotune")
+    ap.add_argument("--launch", default=None,
+                    help="fixed launch shapes 'bp_groups,fwd_lanes' (bp_groups -1: scatter) "
+                         "instead of csgd_solver_autotune")
     a = ap.parse_args()
     if a.steps is None:
         a.steps = DEFAULT_STEPS.get(a.workload, 20)
@@ -291,7 +294,11 @@ def run_gpu(args, cfg, world, rank, local):
     # launch shapes for this workload (csgd_solver_autotune, which resets the
     # solver), then the solve as one CUDA graph (reset, every block step, epoch
     # averages): the library's path for repeated solves
-    shapes = None if args.no_autotune else solver.autotune(min(steps, 16))
+    if args.launch:
+        shapes = tuple(int(v) for v in args.launch.split(","))
+        solver.set_launch(*shapes)
+    else:
+        shapes = None if args.no_autotune else solver.autotune(min(steps, 16))
     graph = solver.graph(steps)
 
     def one_solve():
@@ -438,7 +445,9 @@ def run_gpu(args, cfg, world, rank, local):
                    "ms_per_epoch": ms / args.steps / max(1, int(rep["epochs"]))},
         "roofline": roof, "kernels": kernels, "gpu_launches": launches,
         "launch": "one CUDA graph per solve (reset, all block steps, epoch averages)",
-        "launch_shapes": ({"autotuned": True, "view_groups": shapes[0], "lanes_per_ray": shapes[1]}
+        "launch_shapes": ({"autotuned": not args.launch,
+                           "backprojection": "scatter" if shapes[0] == csgd.SCATTER else "gather",
+                           "view_groups": shapes[0], "lanes_per_ray": shapes[1]}
                           if shapes else {"autotuned": False}),
         "kernel_timing": "per-launch CUDA events in a second pass of the same %d solves launched "
                          "kernel by kernel (%.3f ms per solve that way)" % (args.steps, ms_instr / args.steps),

@@ -319,13 +319,17 @@ int32_t csgd_graph_launch(csgd_graph* graph, csgd_stream stream);
 int32_t csgd_graph_destroy(csgd_graph* graph);
 
 /* Launch shapes (the paper has no counterpart: these tune the GPU kernels, not
- * the method).  bp_groups = view groups per backprojection CTA (1..8) and
- * fwd_lanes = lanes per ray of the dual forward (1, 2 or 4); 0 selects the
- * library's model (occupancy-based groups, lanes by ray count).  They change
- * only the order of FP32 partial sums, i.e. results at rounding level.
+ * the method).  bp_groups = view groups per backprojection CTA (1..8) of the
+ * voxel-driven gather, or -1 for the ray-driven scatter backprojection (each
+ * ray walks the tile and adds len * r to 64-bit fixed-point sums with integer
+ * atomics: exact and order-independent, so also deterministic); fwd_lanes =
+ * lanes per ray of the dual forward and of the scatter (1, 2 or 4); 0 selects
+ * the library's model (gather, occupancy-based groups, lanes by ray count).
+ * They change only the rounding of the sums, i.e. results at rounding level.
  *   csgd_solver_set_launch: sets them; CSGD_ERR_INVALID_ARG out of range.
  *   csgd_solver_autotune: times the backprojection for every group count and
- *     then the dual forward for every lane count over the first trial_steps
+ *     the scatter, then the dual forward (plus the scatter, if chosen) for
+ *     every lane count over the first trial_steps
  *     steps of the schedule (kernel time by CUDA events), keeps the fastest
  *     and resets the solver (x = 0, z = 0, r = y, schedule from the seed);
  *     writes the choice to bp_groups / fwd_lanes if non-NULL.  Synchronises. */

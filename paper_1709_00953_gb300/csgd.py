@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libcsgd.so")
 KINDS = {"parallel2d": 0, "fan2d_flat": 1, "fan2d_curved": 2, "cone3d": 3, "custom3d": 4}
 SEQUENTIAL, UNIFORM, IMPORTANCE, MIXED = 0, 1, 2, 3
 SYNC_COLUMN, SYNC_EPOCH = 0, 1
+SCATTER = -1  # bp_groups value of the ray-driven scatter backprojection
 
 
 class CsgdError(RuntimeError):
@@ -419,12 +420,15 @@ class Solver:
         return Graph(h, [self, x_out])
 
     def set_launch(self, bp_groups: int = 0, fwd_lanes: int = 0):
-        """Launch shapes of the kernels (0 = the library's models)."""
+        """Launch shapes of the kernels (0 = the library's models): view groups
+        per gather CTA 1..8, or SCATTER (-1) for the ray-driven backprojection;
+        lanes per ray 1, 2 or 4."""
         _check(load().csgd_solver_set_launch(self.handle, int(bp_groups), int(fwd_lanes)))
 
     def autotune(self, trial_steps: int, stream=None) -> tuple:
         """Times every launch shape over the first trial_steps steps, keeps the
-        fastest and resets the solver; returns (bp_groups, fwd_lanes)."""
+        fastest and resets the solver; returns (bp_groups, fwd_lanes), with
+        bp_groups = SCATTER (-1) if the scatter backprojection won."""
         c, l = ctypes.c_int32(), ctypes.c_int32()
         _check(load().csgd_solver_autotune(self.handle, int(trial_steps), ctypes.byref(c),
                                            ctypes.byref(l), _stream(stream)))

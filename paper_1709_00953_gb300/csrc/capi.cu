@@ -321,6 +321,9 @@ int solver_reset_device(csgd_solver* S, cudaStream_t s) {
     CSGD_CUDA(cudaMemsetAsync(b.counters, 0, sizeof(unsigned) * b.max_slots, s), "counters");
     CSGD_CUDA(cudaMemsetAsync(b.nnz_slot, 0, sizeof(unsigned long long) * b.max_slots, s),
               "slot counters");
+    CSGD_CUDA(cudaMemsetAsync(b.acc, 0, sizeof(unsigned long long) * b.max_slots * b.g_stride, s),
+              "scatter accumulators");
+    CSGD_CUDA(cudaMemsetAsync(b.rmax, 0, sizeof(unsigned) * b.max_slots, s), "max |r|");
     return CSGD_OK;
 }
 
@@ -807,9 +810,9 @@ static int64_t footprint(const csgd_partition* P, const csgd_solver_params* prm,
     b += 4 * (4 * ny);                           // y, r, p, q
     if (prm->sync == CSGD_SYNC_EPOCH) b += 4 * ny;  // pending residual change
     b += 4 * std::max<int64_t>(1, p.z_floats);   // z store
-    b += 8 * (int64_t)(*max_slots) * p.max_tile_voxels;  // (x, g) pairs per slot
+    b += 16 * (int64_t)(*max_slots) * p.max_tile_voxels;  // (x, g) pairs and scatter sums per slot
     b += (int64_t)sizeof(RayRec) * (*max_slots) * (*max_rays);  // ray tables
-    b += 4 * (int64_t)(*max_slots) * (*n_gg + *fwd_blocks) + 20 * (int64_t)(*max_slots);  // partials, mu, counters, nnz
+    b += 4 * (int64_t)(*max_slots) * (*n_gg + *fwd_blocks) + 24 * (int64_t)(*max_slots);  // partials, mu, counters, nnz, max |r|
     return b;
 }
 
@@ -873,6 +876,9 @@ int32_t csgd_solver_create(const csgd_partition* Pc, const csgd_solver_params* p
     ALLOC(b.q, sizeof(float) * S->n_rays, "cudaMalloc(q)");
     ALLOC(b.g, 2 * sizeof(float) * b.max_slots * b.g_stride, "cudaMalloc(x, g pairs)");
     ALLOC(b.gg_part, sizeof(float) * b.max_slots * ng, "cudaMalloc(gg partials)");
+    ALLOC(b.acc, sizeof(unsigned long long) * b.max_slots * b.g_stride,
+          "cudaMalloc(scatter accumulators)");
+    ALLOC(b.rmax, sizeof(unsigned) * b.max_slots, "cudaMalloc(max |r| per slot)");
     ALLOC(b.table, sizeof(RayRec) * b.max_slots * b.table_stride, "cudaMalloc(ray tables)");
     b.qq_stride = b.max_fwd_blocks;  // one q^T q partial per forward CTA
     ALLOC(b.qq_part, sizeof(float) * b.max_slots * b.qq_stride, "cudaMalloc(qq partials)");
@@ -1419,8 +1425,9 @@ int32_t csgd_solver_set_state(csgd_solver* S, const void* buf, int64_t size, csg
 // ---------------------------------------------------------------------------
 int32_t csgd_solver_set_launch(csgd_solver* S, int32_t bp_groups, int32_t fwd_lanes) {
     if (!S) return fail(CSGD_ERR_INVALID_ARG, "NULL solver");
-    if (bp_groups < 0 || bp_groups > kBPMaxChunks)
-        return fail(CSGD_ERR_INVALID_ARG, "view groups must be 0 (model) or 1..8");
+    if (bp_groups < kBPScatter || bp_groups > kBPMaxChunks)
+        return fail(CSGD_ERR_INVALID_ARG,
+                    "view groups must be -1 (scatter), 0 (model) or 1..8");
     if (fwd_lanes != 0 && fwd_lanes != 1 && fwd_lanes != 2 && fwd_lanes != 4)
         return fail(CSGD_ERR_INVALID_ARG, "lanes per ray must be 0 (model), 1, 2 or 4");
     S->bp_groups = bp_groups;
@@ -1429,8 +1436,8 @@ int32_t csgd_solver_set_launch(csgd_solver* S, int32_t bp_groups, int32_t fwd_la
 }
 
 namespace {
-// Device time of the backprojection (kind 0) or dual forward (kind 1) kernels
-// over the first `steps` scheduled steps from a fresh state.
+// Device time of the backprojection (kind 0), the dual forward (kind 1) or both
+// (kind 2) over the first `steps` scheduled steps from a fresh state.
 int trial_ms(csgd_solver* S, int64_t steps, int kind, cudaStream_t s, double* ms) {
     int rc = solver_reset_state(S, s);
     if (rc) return rc;
@@ -1444,7 +1451,7 @@ int trial_ms(csgd_solver* S, int64_t steps, int kind, cudaStream_t s, double* ms
     if (rc == CSGD_OK) rc = csgd_solver_profile_read(S, &t, 1);
     csgd_solver_profile(S, 0);
     if (rc) return rc;
-    *ms = t.ms[kind];
+    *ms = kind == 2 ? t.ms[0] + t.ms[1] : t.ms[kind];
     return CSGD_OK;
 }
 }  // namespace
@@ -1459,19 +1466,22 @@ int32_t csgd_solver_autotune(csgd_solver* S, int64_t trial_steps, int32_t* bp_gr
     int rc = trial_ms(S, trial_steps, 0, s, &ms);  // warm-up (module loading, caches)
     int best_c = 0;
     double best = 0.0;
-    for (int c = 1; rc == CSGD_OK && c <= kBPMaxChunks; ++c) {
-        S->bp_groups = c;
+    // the gather with 1..8 view groups per CTA, then the scatter
+    for (int c = 1; rc == CSGD_OK && c <= kBPMaxChunks + 1; ++c) {
+        S->bp_groups = c <= kBPMaxChunks ? c : kBPScatter;
         rc = trial_ms(S, trial_steps, 0, s, &ms);
         if (rc == CSGD_OK && (best_c == 0 || ms < best)) {
             best = ms;
-            best_c = c;
+            best_c = S->bp_groups;
         }
     }
     S->bp_groups = best_c;
+    // lanes per ray: the dual forward's, which the scatter shares
+    const int kind = best_c == kBPScatter ? 2 : 1;
     int best_l = 0;
     for (int l = 1; rc == CSGD_OK && l <= 4; l *= 2) {
         S->fwd_lanes = l;
-        rc = trial_ms(S, trial_steps, 1, s, &ms);
+        rc = trial_ms(S, trial_steps, kind, s, &ms);
         if (rc == CSGD_OK && (best_l == 0 || ms < best)) {  // l = 1 starts the comparison
             best = ms;
             best_l = l;

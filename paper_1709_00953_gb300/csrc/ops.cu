@@ -259,6 +259,7 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
             hrow[4] = (double)nzs;
         }
         a.sb.counters[slot] = 0u;
+        if (a.sb.rmax) a.sb.rmax[slot] = 0u;  // read by the backprojection only
     }
 }
 
@@ -274,6 +275,7 @@ struct TableArgs {
     const float* r;
     RayRec* table;       // [slot][ray slot]
     int64_t slot_stride;
+    unsigned* rmax;      // [slot] max |r| bits (scatter backprojection), or null
 };
 
 // Line of bin (ku, kv) of the item in tile-centred coordinates: q and 1/d.
@@ -320,14 +322,17 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
         if (k < nr) table_ray<DIM>(G, V, E, tile, it.u0 + k % wu, it.v0 + k / wu, pq[p], pi[p]);
     }
     pdl_wait();  // r and the table buffer belong to earlier kernels until here
+    float rm = 0.f;  // max |r| of this thread's rays
 #pragma unroll
     for (int p = 0; p < kTablePre; ++p) {
         const int k = k0 + p * stride;
         if (k < nr) {
             const int64_t ray = ray_index(G, it.view, it.u0 + k % wu, it.v0 + k / wu);
+            const float rv = __ldg(a.r + ray);
+            rm = fmaxf(rm, fabsf(rv));
             *reinterpret_cast<float4*>(dst[k].a) = make_float4(pq[p][0], pq[p][1], pi[p][0], pi[p][1]);
             *reinterpret_cast<float4*>(dst[k].b) =
-                make_float4(__ldg(a.r + ray), pq[p][2], pi[p][2], __int_as_float((int)ray));
+                make_float4(rv, pq[p][2], pi[p][2], __int_as_float((int)ray));
         }
     }
     for (int k = k0 + kTablePre * stride; k < nr; k += stride) {
@@ -336,9 +341,16 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
         float q[3], inv[3];
         table_ray<DIM>(G, V, E, tile, ku, kv, q, inv);
         const int64_t ray = ray_index(G, it.view, ku, kv);
+        const float rv = __ldg(a.r + ray);
+        rm = fmaxf(rm, fabsf(rv));
         *reinterpret_cast<float4*>(dst[k].a) = make_float4(q[0], q[1], inv[0], inv[1]);
         *reinterpret_cast<float4*>(dst[k].b) =
-            make_float4(__ldg(a.r + ray), q[2], inv[2], __int_as_float((int)ray));
+            make_float4(rv, q[2], inv[2], __int_as_float((int)ray));
+    }
+    if (a.rmax) {
+        // non-negative floats order like their bit patterns
+        const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(rm));
+        if ((threadIdx.x & 31) == 0 && wm) atomicMax(a.rmax + it.slot, wm);
     }
 }
 
@@ -797,6 +809,138 @@ __global__ void __maxnreg__(64) k_backproject_solver(
 }
 
 // ---------------------------------------------------------------------------
+// Ray-driven backprojection (scatter).  Every ray of a slot walks the tile as
+// in the dual forward (same crossings, so the same lengths) and adds len * r_i
+// to a 64-bit fixed-point accumulator of its voxel with an integer atomic: the
+// sum of the slot's FP32 products len * r_i is then exact (below the fixed
+// point's resolution) and independent of the order of the additions, so the
+// result is deterministic.  A conversion pass turns the accumulator into the
+// (x_J, g_J) pairs and the g^T g partials and clears it.  Which of the two
+// backprojections is faster depends on the geometry: the gather evaluates
+// every candidate line of a voxel's window, the scatter only the crossings.
+// ---------------------------------------------------------------------------
+struct ScatterArgs {
+    DevGeom G;
+    const StepDesc* steps;
+    int first;
+    SolverBuffers sb;
+};
+
+// Fixed-point exponent S of a slot (value = round(2^S * len * r)): a line
+// crosses a unit voxel over at most sqrt(3) < 2, so |sum over the slot's rays|
+// <= 2 n_rays max|r| < 2^e, and S = 62 - e keeps every partial sum below 2^62.
+__device__ __forceinline__ int scatter_shift(unsigned rmax_bits, int64_t n_rays) {
+    const float bound = __uint_as_float(rmax_bits) * 2.0f * (float)(n_rays > 1 ? n_rays : 1);
+    int e = 0;
+    frexpf(bound, &e);  // bound < 2^e (e = 0 for bound = 0)
+    return min(100, max(-100, 62 - e));
+}
+
+// 2^k as a float, k in [-126, 127]
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
+template <int DIM, int L>
+__global__ void __maxnreg__(64) k_backproject_scatter(const ScatterArgs a) {
+    pdl_trigger();
+    const DevGeom& G = a.G;
+    const int slot = blockIdx.y;
+    const StepDesc sd = a.steps[a.first + slot];
+    const DevTile t = G.tiles[sd.j];
+    const int nvox = t.n[0] * t.n[1] * t.n[2];
+    pdl_wait();  // the ray table and the slot's max |r| come from the previous kernel
+    unsigned long long* __restrict__ acc = a.sb.acc + (int64_t)slot * a.sb.g_stride;
+    const float sc = pow2f(scatter_shift(a.sb.rmax[slot], sd.n_rays));
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = gid / L;
+    const int sub = (int)(gid % L);
+    int nz = 0;
+    int first_id = -1, last_id = -1;  // voxels of the lane's first and last non-zero
+    if (k < sd.n_rays) {
+        const RayRec* rp = a.sb.table + (int64_t)slot * a.sb.table_stride + k;
+        const float4 ra = *reinterpret_cast<const float4*>(rp->a);
+        const float4 rb = *reinterpret_cast<const float4*>(rp->b);
+        const float q[3] = {ra.x, ra.y, rb.y};
+        const float inv[3] = {ra.z, ra.w, rb.z};
+        const float rs = rb.x * sc;  // round(len * r) * 2^S == round(len * (r * 2^S))
+        Box b = tile_box(t, DIM, 0, t.n[0], t.n[0] * t.n[1]);
+        float tin, tout;
+        if (clip<DIM>(q, inv, b, &tin, &tout)) {
+            const float dt = (tout - tin) * (1.0f / L);
+            const float t0 = sub == 0 ? tin : fmaf((float)sub, dt, tin);
+            const float t1 = sub == L - 1 ? tout : fmaf((float)(sub + 1), dt, tin);
+            auto batch = [&](const int (&id)[kFwdBatch], const float (&ln)[kFwdBatch]) {
+#pragma unroll
+                for (int u = 0; u < kFwdBatch; ++u) {
+                    if (ln[u] > 0.f) {
+                        ++nz;
+                        first_id = first_id < 0 ? id[u] : first_id;
+                        last_id = id[u];
+                        if (rs != 0.f && (unsigned)id[u] < (unsigned)nvox)
+                            atomicAdd(acc + id[u], (unsigned long long)__float2ll_rn(ln[u] * rs));
+                    }
+                }
+            };
+            if constexpr (DIM == 2) walk2_batched<kFwdBatch>(q, inv, b, t0, t1, batch);
+            else walk3_batched<kFwdBatch>(q, inv, b, t0, t1, batch);
+        }
+    }
+    if constexpr (L > 1) {
+        // a lane boundary inside a voxel splits its segment between two lanes:
+        // count that non-zero once (the L lanes of a ray are consecutive lanes
+        // of one warp; a boundary on a voxel face leaves two different voxels)
+        const int prev_last = __shfl_up_sync(0xffffffffu, last_id, 1);
+        if (sub > 0 && first_id >= 0 && first_id == prev_last) --nz;
+    }
+    if (a.sb.nnz_slot) {
+        __shared__ unsigned s_nz[kFwdThreads / 32];
+        const unsigned wn = __reduce_add_sync(0xffffffffu, (unsigned)nz);
+        if ((threadIdx.x & 31) == 0) s_nz[threadIdx.x >> 5] = wn;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long cn = 0;
+            for (int w = 0; w < kFwdThreads / 32; ++w) cn += s_nz[w];
+            if (cn) atomicAdd(a.sb.nnz_slot + slot, cn);
+        }
+    }
+}
+
+constexpr int kConvThreads = 256;
+
+// g_J = h 2^-S acc (one rounding from the exact fixed-point sum), the pairs
+// (x_J, g_J) for the dual forward, a g^T g partial per CTA (FP32 as in the
+// gather), and acc cleared for the next batch.
+__global__ void __launch_bounds__(kConvThreads) k_scatter_convert(const ScatterArgs a) {
+    pdl_trigger();
+    const DevGeom& G = a.G;
+    const int slot = blockIdx.y;
+    const StepDesc sd = a.steps[a.first + slot];
+    const DevTile t = G.tiles[sd.j];
+    const int nvox = t.n[0] * t.n[1] * t.n[2];
+    pdl_wait();
+    const float isc = pow2f(-scatter_shift(a.sb.rmax[slot], sd.n_rays));
+    unsigned long long* acc = a.sb.acc + (int64_t)slot * a.sb.g_stride;
+    float2* gout = reinterpret_cast<float2*>(a.sb.g) + (int64_t)slot * a.sb.g_stride;
+    const float* xt = a.sb.x + t.voff;
+    float gg = 0.f;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += gridDim.x * blockDim.x) {
+        const long long s = (long long)acc[v];
+        acc[v] = 0ull;
+        const float g = __ll2float_rn(s) * isc * G.h;
+        gout[v] = make_float2(xt[v], g);
+        gg = fmaf(g, g, gg);
+    }
+    __shared__ float s_gg[kConvThreads / 32];
+    const float wg = warp_sum_f(gg);
+    if ((threadIdx.x & 31) == 0) s_gg[threadIdx.x >> 5] = wg;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float cg = 0.f;
+        for (int w = 0; w < kConvThreads / 32; ++w) cg += s_gg[w];
+        a.sb.gg_part[(int64_t)slot * a.sb.gg_stride + blockIdx.x] = cg;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // epilogue, averaging, conversions
 // ---------------------------------------------------------------------------
 struct EpiArgs {
@@ -1088,6 +1232,7 @@ cudaError_t launch_backproject_inline(const DevGeom& G, const DevTile& tile,
     ta.r = r;
     ta.table = table;
     ta.slot_stride = 0;
+    ta.rmax = nullptr;
     int64_t max_item = 0;
     for (int k = 0; k < it.n; ++k)
         max_item = std::max<int64_t>(max_item, (int64_t)(it.items[k].u1 - it.items[k].u0) *
@@ -1151,8 +1296,14 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
                          const StepDesc* steps, const BatchLaunch& b, const SolverBuffers& sb,
                          int sm_count, cudaStream_t s, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], s);
+    const bool scatter = b.bp_groups == kBPScatter;
     BPPlan plan = plan_backprojection(G, tile, b.nslots, (b.n_items + b.nslots - 1) / b.nslots,
-                                      sm_count, b.bp_groups);
+                                      sm_count, scatter ? 0 : b.bp_groups);
+    const int L = b.fwd_lanes == 1 || b.fwd_lanes == 2 || b.fwd_lanes == 4
+                      ? b.fwd_lanes : lanes_per_ray(b.max_rays * b.nslots, sm_count);
+    int64_t nb = (b.max_rays * L + kFwdThreads - 1) / kFwdThreads;
+    if (nb < 1) nb = 1;
+    if (nb > sb.max_fwd_blocks || nb > sb.qq_stride) return cudaErrorInvalidValue;
     // 1. g_J = (A_I^J)^T r_I per slot: ray table, then voxel-driven sums
     TableArgs ta;
     ta.G = G;
@@ -1161,24 +1312,50 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     ta.r = sb.r;
     ta.table = sb.table;
     ta.slot_stride = sb.table_stride;
+    ta.rmax = scatter ? sb.rmax : nullptr;
     cudaError_t e = launch_table(G, b.n_items, b.max_item_rays, s, ta, nullptr, items);
     if (e != cudaSuccess) return e;
-    if (plan.blocks > sb.gg_stride) return cudaErrorInvalidValue;
-    BPArgs a;
-    a.G = G;
-    a.first = b.first;
-    a.table = sb.table;
-    a.table_stride = sb.table_stride;
-    a.xt = sb.x;
-    a.gout = sb.g;
-    a.mode = 0;
-    a.accumulate = 0;
-    a.slot_stride = sb.g_stride;
-    a.gg_part = sb.gg_part;
-    a.gg_stride = sb.gg_stride;
-    a.nnz_slot = sb.nnz_slot;
-    e = launch_bp_common(G, plan, b.nslots, s, a, nullptr, items, steps);
-    if (e != cudaSuccess) return e;
+    int n_gg = plan.blocks;
+    if (scatter) {
+        ScatterArgs sa;
+        sa.G = G;
+        sa.steps = steps;
+        sa.first = b.first;
+        sa.sb = sb;
+        dim3 grid((unsigned)nb, b.nslots);
+        if (G.dim == 2) {
+            if (L == 1) e = launch_pdl(k_backproject_scatter<2, 1>, grid, dim3(kFwdThreads), s, sa);
+            else if (L == 2) e = launch_pdl(k_backproject_scatter<2, 2>, grid, dim3(kFwdThreads), s, sa);
+            else e = launch_pdl(k_backproject_scatter<2, 4>, grid, dim3(kFwdThreads), s, sa);
+        } else {
+            if (L == 1) e = launch_pdl(k_backproject_scatter<3, 1>, grid, dim3(kFwdThreads), s, sa);
+            else if (L == 2) e = launch_pdl(k_backproject_scatter<3, 2>, grid, dim3(kFwdThreads), s, sa);
+            else e = launch_pdl(k_backproject_scatter<3, 4>, grid, dim3(kFwdThreads), s, sa);
+        }
+        if (e != cudaSuccess) return e;
+        const int64_t tv = (int64_t)tile.n[0] * tile.n[1] * tile.n[2];
+        n_gg = (int)std::max<int64_t>(1, (tv + kConvThreads - 1) / kConvThreads);
+        if (n_gg > sb.gg_stride) return cudaErrorInvalidValue;
+        e = launch_pdl(k_scatter_convert, dim3((unsigned)n_gg, b.nslots), dim3(kConvThreads), s, sa);
+        if (e != cudaSuccess) return e;
+    } else {
+        if (plan.blocks > sb.gg_stride) return cudaErrorInvalidValue;
+        BPArgs a;
+        a.G = G;
+        a.first = b.first;
+        a.table = sb.table;
+        a.table_stride = sb.table_stride;
+        a.xt = sb.x;
+        a.gout = sb.g;
+        a.mode = 0;
+        a.accumulate = 0;
+        a.slot_stride = sb.g_stride;
+        a.gg_part = sb.gg_part;
+        a.gg_stride = sb.gg_stride;
+        a.nnz_slot = sb.nnz_slot;
+        e = launch_bp_common(G, plan, b.nslots, s, a, nullptr, items, steps);
+        if (e != cudaSuccess) return e;
+    }
     if (ev) cudaEventRecord(ev[1], s);
     // 2. p = A x_J, q = A g_J, ||q||^2, mu
     FwdSolverArgs f;
@@ -1187,13 +1364,8 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     f.steps = steps;
     f.first = b.first;
     f.sync_epoch = b.sync_epoch;
-    f.n_gg = plan.blocks;
+    f.n_gg = n_gg;
     f.sb = sb;
-    const int L = b.fwd_lanes == 1 || b.fwd_lanes == 2 || b.fwd_lanes == 4
-                      ? b.fwd_lanes : lanes_per_ray(b.max_rays * b.nslots, sm_count);
-    int64_t nb = (b.max_rays * L + kFwdThreads - 1) / kFwdThreads;
-    if (nb < 1) nb = 1;
-    if (nb > sb.max_fwd_blocks || nb > sb.qq_stride) return cudaErrorInvalidValue;
     dim3 grid((unsigned)nb, b.nslots);
     if (G.dim == 2) {
         if (L == 1) e = launch_pdl(k_forward_dual<2, 1>, grid, dim3(kFwdThreads), s, f);

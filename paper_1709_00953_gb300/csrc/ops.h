@@ -25,6 +25,7 @@ struct InlineItems {
 constexpr int kFwdThreads = 128;  // threads of a dual-forward CTA (256 and 64 measured slower)
 constexpr int kBPVox = 64;
 constexpr int kBPMaxChunks = 8;  // view groups per CTA at most
+constexpr int kBPScatter = -1;   // bp_groups value selecting the scatter backprojection
 inline int bp_patch(int dim, int axis) { return dim == 2 ? (axis < 2 ? 8 : 1) : 4; }
 inline int bp_blocks(const DevTile& t, int dim) {
     int b = 1;
@@ -73,6 +74,10 @@ struct SolverBuffers {
     float* q;        // A g_J per ray
     float* g;        // (x_J, g_J) pairs per slot, tile-local [slot][g_stride][2]
     float* gg_part;  // [slot][gg_stride]: g^T g per backprojection CTA (FP32)
+    unsigned long long* acc;  // [slot][g_stride]: fixed-point g_J of the scatter
+                              // backprojection (zero between batches)
+    unsigned int* rmax;       // [slot]: bits of max |r| over the batch's rays (zero
+                              // between batches)
     int gg_stride;
     RayRec* table;   // [slot][table_stride]: ray table of the batch
     int64_t table_stride;
@@ -97,7 +102,8 @@ struct BatchLaunch {
     int w_begin, n_items;    // work items of the batch (contiguous)
     int64_t max_item_rays;   // rays of the largest work item
     int sync_epoch;
-    int bp_groups = 0;       // view groups per backprojection CTA (0: occupancy model)
+    int bp_groups = 0;       // view groups per backprojection CTA (0: occupancy model;
+                             // kBPScatter: ray-driven scatter backprojection)
     int fwd_lanes = 0;       // lanes per ray of the dual forward (0: by ray count)
 };
 

@@ -78,7 +78,7 @@ def test_graph_to_pinned_host(mods):
 
 
 def test_launch_shapes_change_rounding_only(mods):
-    """Every launch shape (view groups per backprojection CTA, lanes per ray) gives
+    """Every launch shape (view groups per backprojection CTA or the scatter, lanes per ray) gives
     the same solve to rounding; autotuning picks a valid shape and resets."""
     csgd, batch = mods
     cfg = C.small_fan2d(n=96, views=48, nu=144, tiles=(3, 3), vb=4, du=2)
@@ -97,13 +97,15 @@ def test_launch_shapes_change_rounding_only(mods):
         return x.cpu().numpy().astype(np.float64)
 
     ref = run(0, 0)
-    for c in range(1, 9):
+    for c in list(range(1, 9)) + [csgd.SCATTER]:
         for l in (1, 2, 4):
             x = run(c, l)
             assert np.sqrt(np.mean((x - ref) ** 2)) <= 1e-5 * max(np.abs(ref).max(), 1e-12), (c, l)
     c, l = s.autotune(8)
-    assert 1 <= c <= 8 and l in (1, 2, 4)
+    assert (c == csgd.SCATTER or 1 <= c <= 8) and l in (1, 2, 4)
     with pytest.raises(RuntimeError):
         s.set_launch(9, 0)
+    with pytest.raises(RuntimeError):
+        s.set_launch(-2, 0)
     with pytest.raises(RuntimeError):
         s.set_launch(0, 3)
