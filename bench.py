@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library's launch-shape models instead of csgd_solver_autotune")
     ap.add_argument("--launch", default=None,
-                    help="fixed launch shapes 'bp_groups,fwd_lanes' (bp_groups -1: scatter) "
+                    help="fixed launch shapes, --launch=bp_groups,fwd_lanes (bp_groups -1: scatter) "
                          "instead of csgd_solver_autotune")
     a = ap.parse_args()
     if a.steps is None:

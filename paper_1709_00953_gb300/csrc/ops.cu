@@ -826,14 +826,17 @@ struct ScatterArgs {
     SolverBuffers sb;
 };
 
-// Fixed-point exponent S of a slot (value = round(2^S * len * r)): a line
-// crosses a unit voxel over at most sqrt(3) < 2, so |sum over the slot's rays|
-// <= 2 n_rays max|r| < 2^e, and S = 62 - e keeps every partial sum below 2^62.
-__device__ __forceinline__ int scatter_shift(unsigned rmax_bits, int64_t n_rays) {
-    const float bound = __uint_as_float(rmax_bits) * 2.0f * (float)(n_rays > 1 ? n_rays : 1);
+// Fixed-point exponent S of a slot (term = round(2^S * len * r)): a line
+// crosses a unit voxel over at most sqrt(3) < 2, so every term is below
+// 2 max|r| 2^S < 2^30 with S = 30 - e, 2 max|r| < 2^e, and fits a 32-bit
+// conversion (FP32 pipe; the 64-bit one runs on the slow FP64 pipe).  A voxel
+// sums at most one term per ray of the slot, below 2^30 n_rays < 2^63.  The
+// resolution, 2^-30 of the largest possible term, is far below FP32 rounding.
+__device__ __forceinline__ int scatter_shift(unsigned rmax_bits) {
+    const float bound = __uint_as_float(rmax_bits) * 2.0f;
     int e = 0;
     frexpf(bound, &e);  // bound < 2^e (e = 0 for bound = 0)
-    return min(100, max(-100, 62 - e));
+    return min(100, max(-100, 30 - e));
 }
 
 // 2^k as a float, k in [-126, 127]
@@ -849,7 +852,7 @@ __global__ void __maxnreg__(64) k_backproject_scatter(const ScatterArgs a) {
     const int nvox = t.n[0] * t.n[1] * t.n[2];
     pdl_wait();  // the ray table and the slot's max |r| come from the previous kernel
     unsigned long long* __restrict__ acc = a.sb.acc + (int64_t)slot * a.sb.g_stride;
-    const float sc = pow2f(scatter_shift(a.sb.rmax[slot], sd.n_rays));
+    const float sc = pow2f(scatter_shift(a.sb.rmax[slot]));
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t k = gid / L;
     const int sub = (int)(gid % L);
@@ -861,7 +864,7 @@ __global__ void __maxnreg__(64) k_backproject_scatter(const ScatterArgs a) {
         const float4 rb = *reinterpret_cast<const float4*>(rp->b);
         const float q[3] = {ra.x, ra.y, rb.y};
         const float inv[3] = {ra.z, ra.w, rb.z};
-        const float rs = rb.x * sc;  // round(len * r) * 2^S == round(len * (r * 2^S))
+        const float rs = rb.x * sc;  // (len * r) * 2^S rounds as len * (r * 2^S)
         Box b = tile_box(t, DIM, 0, t.n[0], t.n[0] * t.n[1]);
         float tin, tout;
         if (clip<DIM>(q, inv, b, &tin, &tout)) {
@@ -876,7 +879,8 @@ __global__ void __maxnreg__(64) k_backproject_scatter(const ScatterArgs a) {
                         first_id = first_id < 0 ? id[u] : first_id;
                         last_id = id[u];
                         if (rs != 0.f && (unsigned)id[u] < (unsigned)nvox)
-                            atomicAdd(acc + id[u], (unsigned long long)__float2ll_rn(ln[u] * rs));
+                            atomicAdd(acc + id[u],
+                                      (unsigned long long)(long long)__float2int_rn(ln[u] * rs));
                     }
                 }
             };
@@ -917,7 +921,7 @@ __global__ void __launch_bounds__(kConvThreads) k_scatter_convert(const ScatterA
     const DevTile t = G.tiles[sd.j];
     const int nvox = t.n[0] * t.n[1] * t.n[2];
     pdl_wait();
-    const float isc = pow2f(-scatter_shift(a.sb.rmax[slot], sd.n_rays));
+    const float isc = pow2f(-scatter_shift(a.sb.rmax[slot]));
     unsigned long long* acc = a.sb.acc + (int64_t)slot * a.sb.g_stride;
     float2* gout = reinterpret_cast<float2*>(a.sb.g) + (int64_t)slot * a.sb.g_stride;
     const float* xt = a.sb.x + t.voff;
@@ -925,7 +929,13 @@ __global__ void __launch_bounds__(kConvThreads) k_scatter_convert(const ScatterA
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += gridDim.x * blockDim.x) {
         const long long s = (long long)acc[v];
         acc[v] = 0ull;
-        const float g = __ll2float_rn(s) * isc * G.h;
+        // 64-bit integer to float on the FP32 pipe: the magnitude's high word
+        // times 2^32 plus its low word, rounded in the fused multiply-add
+        // (exact rounding below 2^32, within one ulp above), then the sign
+        const unsigned long long m = s < 0 ? 0ull - (unsigned long long)s : (unsigned long long)s;
+        const float mf = fmaf((float)(unsigned)(m >> 32), 4294967296.0f,
+                              (float)(unsigned)(m & 0xffffffffull));
+        const float g = (s < 0 ? -mf : mf) * isc * G.h;
         gout[v] = make_float2(xt[v], g);
         gg = fmaf(g, g, gg);
     }
