@@ -50,8 +50,8 @@ DEFAULT_STEPS = {"fan2d_512": 250, "parallel2d_64": 250, "cone3d_256": 12, "batc
 # kernel sources they were taken from (hash of ops.cu, device.cuh, common.h);
 # "backproject" is the ray table plus the gather, the unit the bench times.
 NCU_TRAFFIC = {
-    ("fan2d_512_720x768_8x16_importance", "7b90372dcc53e1db"): {
-        "backproject": 2106880 + 435968, "forward_dual": 2529792},
+    ("fan2d_512_720x768_8x16_importance", "df4fd674eb7355f0"): {
+        "backproject": 2106880 + 434176, "forward_dual": 2529280},
 }
 KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/csrc/device.cuh",
                   "paper_1709_00953_gb300/csrc/common.h")
