@@ -1,6 +1,6 @@
 """GPU parity: the CUDA block operators and solver against the FP64 oracle.
 
-Tolerances (derived in DESIGN.md, "Parity and tolerances"):
+Tolerances, and where they come from:
 
 * per ray of a forward product:
   |gpu - oracle| <= 1e-5 * (|A| |v|)  +  TAU_GEOM * h * max|v|
