@@ -38,9 +38,12 @@ Readings where the paper is silent:
   (`step_length`).
 
 Parity: the single-step decrease identity, steepest descent against a dense
-least-squares solve (m = n = 1) and the m = 1 column-action property are pinned
-in ``tests/test_oracle_solver.py``; whole-run trajectories for m, n > 1 are
-pinned by nothing but this code (the paper prints no trajectory).
+least-squares solve (m = n = 1), the m = 1 column-action property (r = y - A x
+exactly after every epoch, across tiles), the epoch mean of candidates, and
+whole runs with m = 8 row blocks and n = 2 tiles reaching the exact solution of
+a consistent full-rank problem (importance and uniform sampling) are pinned in
+``tests/test_oracle_solver.py``.  The paper prints no trajectory to compare a
+run with step by step.
 """
 from __future__ import annotations
 

@@ -141,3 +141,39 @@ def test_step_length_one_entry_block_and_rounding_support():
         g = ln * r
         q = ln * g
         assert step_length(beta, g * g, q * q, h) == 0.0
+
+
+def _split_cone():
+    """A cone scan whose volume is split at the source's plane into two tiles and
+    whose detector is split at the same height: a line that reaches the upper
+    half of the detector never enters the lower tile (it leaves the source's
+    plane upward and stays above it), so A is block diagonal in (I, J) and P
+    has exact zeros off the diagonal blocks."""
+    g = Geometry("cone3d", (4, 4, 2), 1.0, uniform_angles(16, 360), nu=8, nv=8, pu=1.0, pv=1.0,
+                 sod=12.0, sdd=24.0)
+    part = Partition(g, tiles=(1, 1, 2), view_blocks=4, det_blocks=(1, 2))
+    org, d = g.rays()
+    A = siddon.system_matrix(g.grid, org, d).toarray()
+    assert np.linalg.matrix_rank(A) == A.shape[1]
+    return part, A
+
+
+@pytest.mark.parametrize("sampling,b,epochs,tol", [(S.IMPORTANCE, 1.0, 300, 1e-8),
+                                                   (S.UNIFORM, 2.0, 300, 1e-4)])
+def test_many_blocks_reach_the_exact_solution(sampling, b, epochs, tol):
+    """m = 8 row blocks (4 view groups x 2 detector halves), n = 2 tiles, the
+    column batches, z store, residual refresh and candidate averages of Alg. 3
+    over many epochs: on consistent data y = A x* with A of full column rank,
+    every step's direction lies in the block's row space and the fixed point
+    has r = 0, so the run must reach x*.  Uniform sampling also draws the
+    zero-overlap blocks (their candidates x_J count in the mean)."""
+    from oracle.ptable import probability_table
+    part, A = _split_cone()
+    P = probability_table(part)
+    for i in range(P.shape[0]):
+        upper = part.row_block_parts(i)[1] == 1  # row block i reads the upper half
+        assert P[i, 0 if upper else 1] == 0.0 and P[i, 1 if upper else 0] > 0.2
+    x_star = np.random.default_rng(3).random(A.shape[1])
+    sol = OracleSolver(part, dict(sampling=sampling, alpha=1.0, b=b, seed=5), A @ x_star)
+    x = sol.run_epochs(epochs)
+    assert np.max(np.abs(x - x_star)) < tol
