@@ -50,7 +50,7 @@ DEFAULT_STEPS = {"fan2d_512": 250, "parallel2d_64": 250, "cone3d_256": 12, "batc
 # kernel sources they were taken from (hash of ops.cu, device.cuh, common.h);
 # "backproject" is the ray table plus the gather, the unit the bench times.
 NCU_TRAFFIC = {
-    ("fan2d_512_720x768_8x16_importance", "df4fd674eb7355f0"): {
+    ("fan2d_512_720x768_8x16_importance", "1d8614d2283f6cae"): {
         "backproject": 2106880 + 434176, "forward_dual": 2529280},
 }
 KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/csrc/device.cuh",
@@ -58,10 +58,17 @@ KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/
 
 
 def kernel_hash() -> str:
+    """Hash of the kernel sources without comments and blank lines: a change
+    of the code voids the stored traffic figures, a change of a comment not."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        src = open(os.path.join(ROOT, f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        lines = [ln.rstrip() for ln in src.splitlines() if ln.strip()]
+        h.update("\n".join(lines).encode())
     return h.hexdigest()[:16]
 
 

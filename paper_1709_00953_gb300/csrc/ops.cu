@@ -3,14 +3,19 @@
 //   k_project_inline  z_I = A_I^J x_J for the stand-alone operator: ray-driven
 //                     incremental walk, 1-4 lanes per ray.
 //   k_ray_table_*     per launch, the line (tile-centred point q, 1/d) and the
-//                     residual r of every ray of every slot, set up once.
+//                     residual r of every ray of every slot, set up once (and
+//                     max |r| per slot for the scatter).
 //   k_backproject_*   g_J = (A_I^J)^T r_I (Eq. 'direction'): voxel-driven gather
 //                     over the ray table (each voxel sums len * r over the bins
 //                     of its shadow), the partial sums of a CTA's view groups
-//                     added in shared memory in a fixed order, g^T g in FP64.
+//                     added in shared memory in a fixed order, g^T g per CTA.
 //                     No atomics.
-//   k_forward_dual    p = A x_J and q = A g_J in one walk per ray, ||q||^2 in
-//                     FP64, the step length mu computed by the last CTA of each
+//   k_backproject_scatter + k_scatter_convert
+//                     the same g_J ray-driven: every ray walks the tile and adds
+//                     len * r to 64-bit fixed-point sums with integer atomics
+//                     (exact, order-independent), then one pass converts them.
+//   k_forward_dual    p = A x_J and q = A g_J in one walk per ray, ||q||^2 per
+//                     CTA, the step length mu computed by the last CTA of each
 //                     slot (Alg. 1, Eq. 'step').
 //   k_epilogue        z_I^j = p + mu q, r -= z_new - z_old (the refresh of
 //                     Alg. 2-4 applied incrementally), x^_J += x_J + mu g_J.
@@ -127,14 +132,15 @@ __global__ void __launch_bounds__(kFwdThreads) k_project_inline(
     forward_single<DIM, L>(G, it.items, it.step, x, out, accumulate);
 }
 
-// p = A x_J and q = A g_J for every ray of a slot in one walk (z = p + mu q by
-// linearity), with ||q||^2 in FP64.  Rays come from the batch's ray table (set
-// up once for the backprojection), split over L lanes by parameter range.  Each
-// CTA writes its partial sums; the last CTA of the slot to finish adds them in a
-// fixed order and computes mu = beta g^T g / q^T q (no grid barrier).
 // (2^-12)^2: the smallest squared gain ||A g||^2 / (h^2 ||g||^2) of a step
 constexpr double kMinGain2 = 5.9604644775390625e-08;
 
+// p = A x_J and q = A g_J for every ray of a slot in one walk (z = p + mu q by
+// linearity), with ||q||^2.  Rays come from the batch's ray table (set up once
+// for the backprojection), split over L lanes by parameter range.  Each CTA
+// writes its partial sum of squares (FP32); the last CTA of the slot to finish
+// adds them in a fixed order (exactly as FP32 pairs, then in FP64) and computes
+// mu = beta g^T g / q^T q (no grid barrier).
 template <int DIM, int L>
 __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     pdl_trigger();
@@ -213,7 +219,7 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     }
     // per-CTA partials in FP32 (the squares, a warp tree, then the warps in
     // order: within 9 u of the CTA's exact sum of squares), then the last CTA
-    // of the slot to finish adds the partials in FP64 in a fixed order
+    // of the slot to finish adds the partials in a fixed order
     __shared__ double s_q[kFwdThreads / 32];
     __shared__ float s_qf[kFwdThreads / 32];
     __shared__ unsigned s_last;
