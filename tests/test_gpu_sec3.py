@@ -105,3 +105,22 @@ def test_group_size_one_all_blocks_matches_oracle(X, problem):
     np.testing.assert_allclose(mu_g[ok], mu_o[ok], rtol=1e-5, atol=0.0)
     np.testing.assert_allclose(mu_g, mu_o, rtol=1e-2, atol=0.0)
     assert float(np.sqrt(np.mean((x.cpu().numpy() - xo) ** 2))) <= 1e-4
+
+
+def test_sampling_trends_of_sec3d(X, problem):
+    """Sec. III-D: density-weighted (importance) sampling converges faster than
+    uniform sampling for small groups; for groups of 100 it leads only early
+    on, and mixed sampling keeps its early rate and ends with uniform's."""
+    from paper_1709_00953_gb300 import csgd
+
+    def snr(s, b, sampling, eff):
+        return _snr_at(problem.run(b=b, alpha=0.5, group_size=s, sampling=sampling,
+                                   eff_epochs=eff), eff)
+    assert snr(5, 25.0, csgd.IMPORTANCE, 10) > snr(5, 25.0, csgd.UNIFORM, 10) + 2.0
+    imp = problem.run(b=2.0, alpha=0.5, group_size=100, sampling=csgd.IMPORTANCE, eff_epochs=50)
+    uni = problem.run(b=2.0, alpha=0.5, group_size=100, sampling=csgd.UNIFORM, eff_epochs=50)
+    mix = problem.run(b=2.0, alpha=0.5, group_size=100, sampling=csgd.MIXED, eff_epochs=50)
+    assert _snr_at(imp, 5) > _snr_at(uni, 5) + 3.0
+    assert abs(_snr_at(mix, 5) - _snr_at(imp, 5)) < 2.0
+    assert _snr_at(uni, 50) > _snr_at(imp, 50) + 10.0
+    assert _snr_at(mix, 50) > _snr_at(imp, 50) + 10.0
