@@ -152,3 +152,23 @@ def test_sec3_study_step_counts(lib):
     counts = X.groups_per_epoch(flat, 3)
     assert counts == [sum(len(g) for _, g in ep) for ep in eps]
     assert all(c > 0 for c in counts)
+
+
+def test_explicit_view_sets_match_oracle(lib):
+    """Row blocks over arbitrary view sets (Eq. e1 allows any index sets): an
+    interleaved map view -> block gives the oracle's P table and schedule."""
+    cfg = C.small_fan2d(n=64, views=30, nu=96, tiles=(2, 2), vb=3, du=2)
+    vbo = [v % 3 for v in range(30)]
+    g = lib.Geometry(cfg["geom"])
+    p = lib.Partition(g, tiles=(2, 2), view_block_of=vbo, det_blocks=(2, 1))
+    og = OGeom(**cfg["geom"])
+    op = OPart(og, (2, 2), det_blocks=(2, 1), view_block_of=vbo)
+    assert (p.m, p.n) == (op.n_row_blocks, op.n_col_blocks) == (6, 4)
+    P = OP.probability_table(op)
+    np.testing.assert_allclose(p.probabilities(), P, rtol=1e-12, atol=1e-15)
+    prm = dict(cfg["solver"], sampling=2, alpha=0.5, group_size=2, seed=21)
+    flat = lib.schedule_generate(p, prm, 3)
+    rng = OS.SplitMix64(prm["seed"])
+    vb = [op.row_block_parts(i)[0] for i in range(op.n_row_blocks)]
+    eps = [OS.epoch_schedule(rng, P, prm, e, vb) for e in range(3)]
+    assert flat == OS.flatten(eps)
