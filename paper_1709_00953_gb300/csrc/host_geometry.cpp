@@ -41,6 +41,11 @@ int geometry_from_desc(const csgd_geometry_desc* d, Geometry* g, std::string* er
             *err = "voxel counts must be in [1, 65536]";
             return CSGD_ERR_INVALID_ARG;
         }
+    // the kernels index voxels (and a tile's voxels) with 32-bit integers
+    if ((int64_t)g->n[0] * g->n[1] * g->n[2] >= ((int64_t)1 << 31)) {
+        *err = "too many voxels (the grid must hold fewer than 2^31)";
+        return CSGD_ERR_INVALID_ARG;
+    }
     if (!(d->h > 0) || !std::isfinite(d->h)) {
         *err = "voxel edge h must be positive";
         return CSGD_ERR_INVALID_ARG;

@@ -119,6 +119,13 @@ def test_invalid_arguments_are_rejected(lib):
     bad_fan = dict(C.small_fan2d()["geom"], sod=10.0)
     with pytest.raises(csgd.CsgdError):
         csgd.Geometry(bad_fan)
+    # 1291^3 voxels (8.6 GB of FP32) is more than 32-bit voxel indices reach
+    big = dict(C.cone3d_256()["geom"], n=(1291, 1291, 1291), sod=4000.0, sdd=8000.0)
+    with pytest.raises(csgd.CsgdError) as e:
+        csgd.Geometry(big)
+    assert e.value.code == -1 and "voxels" in str(e.value)
+    ok = dict(C.cone3d_256()["geom"], n=(1290, 1290, 1290), sod=4000.0, sdd=8000.0)
+    csgd.Geometry(ok)  # 2,146,689,000 < 2^31
 
 
 def test_footprint_grows_with_problem(lib):
