@@ -29,13 +29,8 @@ Readings where the paper is silent:
   drawn so far, then averaging); the next run starts a fresh epoch.
 * A block drawn with zero overlap (possible under uniform sampling) gives
   g = 0, mu = 0 and a candidate equal to x_J, which is counted in the mean.
-* The exact line search divides by ||A g||^2.  A block whose only support is
-  rounding-level (a line through a tile corner, which the exact geometry gives
-  length 0 and a rounded one a length of order 1e-6 h) would get mu ~ 1 / len^2
-  and throw x_J far off.  The step is therefore skipped (mu = 0) when the gain
-  ||A g|| / ||g|| is below 2^-12 h: genuine support has lengths of order h
-  along g, rounding noise stays orders of magnitude below the bound
-  (`step_length`).
+  More generally mu = 0 whenever A g = 0 (Eq. 'step' is undefined there and
+  the step direction has no effect on the block's rows).
 
 Parity: the single-step decrease identity, steepest descent against a dense
 least-squares solve (m = n = 1), the m = 1 column-action property (r = y - A x
@@ -55,15 +50,9 @@ from .ptable import probability_table
 
 COLUMN, EPOCH = 0, 1
 
-# Smallest gain ||A_I^J g|| / ||g|| (in units of the voxel size h) for which
-# the exact line search is taken; below it mu = 0.
-MIN_GAIN = 2.0 ** -12
-
-
-def step_length(beta: float, gg: float, qq: float, h: float) -> float:
-    """mu = beta g^T g / ||A g||^2 (Eq. 'step'), or 0 when ||A g||^2 is at most
-    (MIN_GAIN h)^2 g^T g (no step on rounding-level support, including A g = 0)."""
-    if qq > (MIN_GAIN * h) ** 2 * gg:
+def step_length(beta: float, gg: float, qq: float) -> float:
+    """mu = beta g^T g / ||A g||^2 (Eq. 'step'), and 0 when A g = 0."""
+    if qq > 0.0:
         return beta * gg / qq
     return 0.0
 
@@ -159,7 +148,7 @@ class OracleSolver:
         gg = float(np.dot(gJ, gJ))
         qq = float(np.dot(q, q))
         beta = self.p["b"] * float(sum(self.P[i, j] for i in group))
-        mu = step_length(beta, gg, qq, part.geom.h)
+        mu = step_length(beta, gg, qq)
         c = np.zeros_like(self.x)
         c[vox] = self.x[vox] + mu * gJ
         self.xhat[vox] += c[vox]

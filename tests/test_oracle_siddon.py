@@ -223,3 +223,61 @@ def test_parallel_projection_of_disc():
     # a half-bin shift of the bin centres would be far worse
     ref_shift = np.tile(2 * np.sqrt(np.maximum(a * a - (s + 0.35) ** 2, 0)), 6)
     assert np.sqrt(np.mean((p - ref_shift) ** 2)) > 3 * np.sqrt(np.mean((p - ref) ** 2))
+
+
+def _rel_rms(a, b):
+    return np.sqrt(np.mean((a - b) ** 2)) / np.sqrt(np.mean(b ** 2))
+
+
+def test_flat_fan_line_integrals_converge():
+    """The flat-detector fan (the Sec. III scan's detector) against exact line
+    integrals along synth's own rays: O(h) convergence, and a mirrored detector
+    (u axis reversed) or the opposite rotation sense is far off."""
+    spec = dict(kind="fan2d_flat", angles=uniform_angles(10, 360) + 0.1, nu=48, pu=0.9,
+                sod=40.0, sdd=80.0)
+    width = 24.0
+    ph = PH.make_phantom(2, 5, width / 2, seed=21)
+    exact = PH.line_integrals(ph, *PH.rays_of(spec))
+    errs = []
+    for n in (24, 48, 96):
+        h = width / n
+        g = Geometry("fan2d_flat", (n, n), h, spec["angles"], nu=48, pu=0.9, sod=40.0, sdd=80.0)
+        xh = PH.pixelize(ph, (n, n), h, sub=8)
+        A = siddon.system_matrix(g.grid, *g.rays())
+        errs.append(_rel_rms(A @ xh, exact))
+    assert errs[0] < 0.1
+    assert errs[1] < 0.7 * errs[0] and errs[2] < 0.7 * errs[1]
+    p = A @ xh
+    mirrored = PH.line_integrals(ph, *PH.rays_of(dict(spec, pu=-spec["pu"])))
+    assert _rel_rms(p, mirrored) > 10 * errs[2]
+    reversed_sense = PH.line_integrals(ph, *PH.rays_of(dict(spec, angles=-spec["angles"])))
+    assert _rel_rms(p, reversed_sense) > 10 * errs[2]
+
+
+def test_custom_pose_line_integrals_converge():
+    """Arbitrary per-view poses (Sec. III-E, random spherical orbit): the oracle's
+    lines through C + u e_u + v e_v from S against exact line integrals along
+    synth's own rays of the same poses; a detector with e_u mirrored, or with
+    e_u and e_v swapped, is far off."""
+    from synth.configs import random_sphere_poses
+    poses = random_sphere_poses(6, 30.0, 60.0, seed=5)
+    spec = dict(kind="custom3d", poses=poses, nu=20, nv=16, pu=1.7, pv=1.9)
+    width = 16.0
+    ph = PH.make_phantom(3, 4, width / 2, seed=22)
+    exact = PH.line_integrals(ph, *PH.rays_of(spec))
+    errs = []
+    for n in (16, 32):
+        h = width / n
+        g = Geometry("custom3d", (n, n, n), h, nu=20, nv=16, pu=1.7, pv=1.9, poses=poses)
+        xh = PH.pixelize(ph, (n, n, n), h, sub=4)
+        A = siddon.system_matrix(g.grid, *g.rays())
+        errs.append(_rel_rms(A @ xh, exact))
+    assert errs[0] < 0.35
+    assert errs[1] < 0.6 * errs[0]
+    p = A @ xh
+    mir = poses.copy()
+    mir[:, 6:9] *= -1.0
+    assert _rel_rms(p, PH.line_integrals(ph, *PH.rays_of(dict(spec, poses=mir)))) > 4 * errs[1]
+    swp = poses.copy()
+    swp[:, 6:9], swp[:, 9:12] = poses[:, 9:12], poses[:, 6:9]
+    assert _rel_rms(p, PH.line_integrals(ph, *PH.rays_of(dict(spec, poses=swp)))) > 4 * errs[1]

@@ -124,23 +124,62 @@ def test_metrics_closed_forms():
     assert metrics.rmse([1, 2, 3], [1, 2, 5]) == pytest.approx(np.sqrt(4 / 3))
 
 
-def test_step_length_one_entry_block_and_rounding_support():
+def test_observation_gap_closed_forms():
+    """Sec. III's observation gap 20 log10(||y|| / ||y - A x||) on a 2 x 2 image
+    seen by two horizontal parallel rays through the pixel rows (view angle 0,
+    bins at +-1/2): A x = (x00 + x10, x01 + x11) with unit lengths.  x = (1, 2,
+    3, 4) gives A x = (3, 7); y = (4, 7) leaves the residual (1, 0), so the gap
+    is 20 log10(sqrt(65)) = 10 log10(65).  Consistent data y = A x gives an
+    infinite gap, and x = 0 gives 0 dB."""
+    g = Geometry("parallel2d", (2, 2), 1.0, np.array([0.0]), nu=2, pu=1.0)
+    x = np.array([1.0, 2.0, 3.0, 4.0])
+    np.testing.assert_allclose(metrics.forward_full(g, x), [3.0, 7.0], rtol=0, atol=1e-14)
+    assert metrics.observation_gap_db(g, [4.0, 7.0], x) == pytest.approx(10 * np.log10(65.0),
+                                                                          rel=1e-14)
+    with np.errstate(divide="ignore"):
+        assert metrics.observation_gap_db(g, [3.0, 7.0], x) == np.inf
+    assert metrics.observation_gap_db(g, [4.0, 7.0], np.zeros(4)) == pytest.approx(0.0, abs=1e-12)
+
+
+def test_step_length_one_entry_block():
     """Eq. 'step' on a one-entry block A = [l]: g = l r and q = A g = l^2 r, so
-    mu = beta / l^2, and with beta = 1 the step solves the row exactly.  Support
-    below the gain floor 2^-12 h (rounding noise, e.g. a line through a tile
-    corner) takes no step."""
-    from oracle.solver import MIN_GAIN, step_length
-    h, r, beta = 0.5, 3.0, 0.7
-    assert MIN_GAIN == 2.0 ** -12
-    for ln in (0.8 * h, 0.01 * h, 1e-3 * h):
+    mu = beta / l^2 for every l > 0, however small (no floor on the gain), and
+    with beta = 1 the step solves the row exactly.  A g = 0 takes no step."""
+    from oracle.solver import step_length
+    r, beta = 3.0, 0.7
+    for ln in (0.8, 0.01, 1e-3, 1e-5, 1e-9):
         g = ln * r
         q = ln * g
-        assert step_length(beta, g * g, q * q, h) == pytest.approx(beta / ln ** 2, rel=1e-14)
-        assert r - step_length(1.0, g * g, q * q, h) * q == pytest.approx(0.0, abs=1e-12 * r)
-    for ln in (1e-5 * h, 1e-9 * h, 0.0):
-        g = ln * r
-        q = ln * g
-        assert step_length(beta, g * g, q * q, h) == 0.0
+        assert step_length(beta, g * g, q * q) == pytest.approx(beta / ln ** 2, rel=1e-14)
+        assert r - step_length(1.0, g * g, q * q) * q == pytest.approx(0.0, abs=1e-12 * r)
+    assert step_length(beta, 0.0, 0.0) == 0.0
+    assert step_length(beta, 1.0, 0.0) == 0.0
+
+
+def test_line_through_tile_corner_has_no_support():
+    """A line through a corner of a tile meets it in a point: the block it
+    forms with a detector sub-area that sees the tile only there has A_I^J = 0
+    exactly (no structural sliver from rounding), so g = 0, q = 0 and mu = 0.
+    Odd detector (bin 4 of 9 on the central ray) through the grid centre, which
+    is a corner of all four tiles, at view angles that are not multiples of 90
+    degrees."""
+    from oracle.geometry import Geometry, uniform_angles
+    g = Geometry("fan2d_flat", (8, 8), 1.0, uniform_angles(36, 360), nu=9, pu=1.0, sod=20.0,
+                 sdd=40.0)
+    part = Partition(g, tiles=(2, 2), view_blocks=36, det_blocks=(9, 1))
+    for v in (1, 5, 13, 22, 31):
+        i = v * 9 + 4  # view v, sub-area = bin 4 alone
+        for j in range(4):
+            rows, z = project_block(part, [i], j, np.ones(g.grid.size))
+            if np.any(z > 0):
+                assert z.max() > 1.0  # the line crosses this tile's interior
+            else:
+                gvec = backproject_block(part, [i], j, np.ones(rows.size))
+                assert not np.any(gvec)
+        # the central line crosses exactly two of the four tiles' interiors
+        crossed = [j for j in range(4)
+                   if np.any(project_block(part, [i], j, np.ones(g.grid.size))[1] > 0)]
+        assert len(crossed) == 2, (v, crossed)
 
 
 def _split_cone():
