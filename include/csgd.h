@@ -256,6 +256,9 @@ typedef struct {
     double updates;        /* ray-voxel updates = 3 * nnz (one backprojection and
                               two forward products per non-zero)                  */
     double residual_norm;  /* ||y - A x|| (FP64), only if compute_residual       */
+    int64_t rays;          /* sum over the steps of the rays of I_g that can meet
+                              tile J (the rows a step reads r and writes z on)    */
+    int64_t tile_voxels;   /* sum over the steps of the voxels of tile J          */
 } csgd_report;
 
 /* Runs n_steps steps of the schedule, then closes the epoch (refresh and

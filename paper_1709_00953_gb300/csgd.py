@@ -80,7 +80,8 @@ KERNEL_KINDS = ("backproject", "forward_dual", "epilogue", "epoch_close")
 
 class Report(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("epochs", ctypes.c_int64), ("nnz", ctypes.c_int64),
-                ("updates", ctypes.c_double), ("residual_norm", ctypes.c_double)]
+                ("updates", ctypes.c_double), ("residual_norm", ctypes.c_double),
+                ("rays", ctypes.c_int64), ("tile_voxels", ctypes.c_int64)]
 
 
 # every symbol include/csgd.h declares, with its signature
@@ -398,7 +399,7 @@ class Solver:
         if not report:
             return None
         return dict(steps=rep.steps, epochs=rep.epochs, nnz=rep.nnz, updates=rep.updates,
-                    residual_norm=rep.residual_norm)
+                    residual_norm=rep.residual_norm, rays=rep.rays, tile_voxels=rep.tile_voxels)
 
     def history(self, capacity: int = 1 << 20) -> list:
         cnt = ctypes.c_int64(0)

@@ -65,25 +65,32 @@ int ensure_device(csgd_partition* P) {
     CSGD_CUDA(cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, dev),
               "cudaDeviceGetAttribute");
     size_t bv = sizeof(DevView) * p.views_h.size();
+    size_t bv64 = sizeof(DevView64) * p.views64_h.size();
     size_t bt = sizeof(DevVT) * p.vt_h.size();
     size_t bti = sizeof(DevTile) * p.tiles_h.size();
     cudaError_t e = cudaMalloc(&p.d_views, bv);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_views64, bv64);
     if (e == cudaSuccess) e = cudaMalloc(&p.d_vt, bt);
     if (e == cudaSuccess) e = cudaMalloc(&p.d_tiles, bti);
     if (e == cudaSuccess) e = cudaMemcpy(p.d_views, p.views_h.data(), bv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p.d_views64, p.views64_h.data(), bv64, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p.d_vt, p.vt_h.data(), bt, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p.d_tiles, p.tiles_h.data(), bti, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         // leave the partition as it was: nothing on the device
         cudaFree(p.d_views);
+        cudaFree(p.d_views64);
         cudaFree(p.d_vt);
         cudaFree(p.d_tiles);
         p.d_views = nullptr;
+        p.d_views64 = nullptr;
         p.d_vt = nullptr;
         p.d_tiles = nullptr;
         return cuda_fail(e, "upload partition tables");
     }
     p.dg.views = p.d_views;
+    p.dg.views64 = p.d_views64;
     p.dg.vt = p.d_vt;
     p.dg.tiles = p.d_tiles;
     P->on_device = true;
@@ -595,6 +602,7 @@ int32_t csgd_partition_destroy(csgd_partition* P) {
     if (!P) return CSGD_OK;
     if (P->on_device) {
         cudaFree(P->p.d_views);
+        cudaFree(P->p.d_views64);
         cudaFree(P->p.d_vt);
         cudaFree(P->p.d_tiles);
     }
@@ -992,6 +1000,12 @@ int32_t csgd_solve(csgd_solver* S, int64_t n_steps, float* x_out, int32_t x_on_h
     plan_scheduled(S, &pl, n_steps, true);
     int rc = execute_plan(S, pl, s);
     if (rc) return rc;
+    int64_t rays = 0, tile_voxels = 0;
+    for (const StepDesc& sd : pl.steps) {
+        const DevTile& t = p.tiles_h[sd.j];
+        rays += sd.n_rays;
+        tile_voxels += (int64_t)t.n[0] * t.n[1] * t.n[2];
+    }
     if (x_out) {
         if (x_on_host) {
             if (!S->d_xrow) {
@@ -1039,6 +1053,8 @@ int32_t csgd_solve(csgd_solver* S, int64_t n_steps, float* x_out, int32_t x_on_h
         report->epochs = S->epoch;
         report->nnz = (int64_t)(nnz1 - nnz0);
         report->updates = 3.0 * (double)(nnz1 - nnz0);
+        report->rays = rays;
+        report->tile_voxels = tile_voxels;
     }
     return CSGD_OK;
 }

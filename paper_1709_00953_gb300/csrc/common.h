@@ -29,6 +29,14 @@ struct DevView {
     float pad[3];
 };
 
+// Per view, FP64, voxel units: the same frame as DevView before rounding.
+// Used only for the exact-geometry check of lines that the FP32 set-up finds
+// grazing a tile's edge (see touches_only in device.cuh).
+struct DevView64 {
+    double S[3], dc[3], eu[3], ev[3];
+    double sdd;
+};
+
 struct DevVT {
     float B[3];    // Q(k0u, k0v) - T: tile-centred point on the reference ray
     float U[3];    // Q step per u bin (flat / parallel); curved: U[0] = depth of
@@ -66,7 +74,9 @@ struct DevGeom {
     float cu, cv;          // (nu-1)/2, (nv-1)/2
     float inv_pu, inv_pv;  // 1 / pu, 1 / pv
     float h;               // voxel edge (world units): lengths are scaled by h
+    double pu_d, pv_d;     // pu, pv in FP64
     const DevView* views;
+    const DevView64* views64;
     const DevVT* vt;       // [view][tile]
     const DevTile* tiles;
 };

@@ -94,6 +94,105 @@ __device__ __forceinline__ bool clip(const float q[3], const float inv[3], const
     return t0 < t1;
 }
 
+// ---------------------------------------------------------------------------
+// Lines that only touch a tile.  A line through a corner of a tile (2D) or
+// along one of its edges (3D) meets it in exact geometry with length 0, so it
+// gives the block A_I^J no entry (the FP64 oracle's Siddon drops such gaps as
+// structural zeros).  The FP32 set-up places a line to about 1e-5 voxel, and
+// may clip a sliver off the tile instead: of length up to ~1e-5 / sin(phi) for
+// a line at angle phi to the axes.  A block whose only support is such
+// slivers (a detector sub-area that meets the tile's shadow only at its edge,
+// with a bin centre exactly on that edge) would get q = A g of the order of the
+// sliver length squared times r and an exact line search mu ~ 1 / length^2.
+// So whenever the FP32 clip enters and leaves the tile through faces of two
+// different axes and its extent along one of them is below kSliverExtent (a
+// hundred times the FP32 placement error), the chord is recomputed in FP64 from
+// the unrounded frame, and a line whose exact chord is at most kTouchChord has
+// no support in the tile.  Lines with a genuine chord are left as they are.
+// ---------------------------------------------------------------------------
+constexpr float kSliverExtent = 1.0f / 1024.0f;
+constexpr double kTouchChord = 1e-9;  // voxel units
+// q[0] of a line that has no support in the tile: every slab of the tile is
+// then empty for it (clip fails, slab clips give length 0)
+constexpr float kNoSupport = 1e30f;
+
+// The clip of `clip` that also reports whether the chord [tin, tout] is an
+// edge sliver (entry and exit faces of different axes, extent along one of
+// them below kSliverExtent).  Same arithmetic as clip.
+template <int DIM>
+__device__ __forceinline__ bool clip_sliver(const float q[3], const float inv[3], const Box& b,
+                                            float* tin, float* tout, bool* sliver) {
+    float t0 = -INFINITY, t1 = INFINITY;
+    float e0 = 0.f, e1 = 0.f;  // |1/d| of the entry and exit axes
+    bool in_set = false, out_set = false;
+    int ain = -1, aout = -1;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        if (isfinite(inv[a])) {
+            float ta = (b.lo[a] - q[a]) * inv[a];
+            float tb = (b.lo[a] + (float)b.n[a] - q[a]) * inv[a];
+            const float lo = fminf(ta, tb), hi = fmaxf(ta, tb);
+            if (lo > t0) { t0 = lo; e0 = fabsf(inv[a]); ain = a; in_set = true; }
+            if (hi < t1) { t1 = hi; e1 = fabsf(inv[a]); aout = a; out_set = true; }
+        } else if (!(q[a] >= b.lo[a] && q[a] < b.lo[a] + (float)b.n[a])) {
+            *sliver = false;
+            return false;
+        }
+    }
+    *tin = t0;
+    *tout = t1;
+    const float L = t1 - t0;
+    *sliver = in_set && out_set && ain != aout && fminf(L / e0, L / e1) < kSliverExtent;
+    return t0 < t1;
+}
+
+// Chord (voxel units) of the exact line of bin (ku, kv) of view `view` through
+// tile t, from the FP64 frame (the line the per (view, tile) FP32 constants
+// round); at most 0 when the line misses the tile.  Half-open faces as in the
+// walk: a line parallel to an axis meets the tile when lo <= q < hi.
+__device__ __forceinline__ double exact_chord(const DevGeom& G, int view, int ku, int kv,
+                                           const DevTile& t) {
+    const DevView64& V = G.views64[view];
+    double p0[3], d[3];
+    if (G.kind == PARALLEL_2D) {
+        const double s = ((double)ku - (double)G.cu) * G.pu_d;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            p0[a] = s * V.eu[a] - (double)t.T[a];
+            d[a] = V.dc[a];
+        }
+    } else if (G.kind == FAN_2D_CURVED) {
+        double sg, cg;
+        sincos(((double)ku - (double)G.cu) * G.pu_d, &sg, &cg);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            p0[a] = V.S[a] - (double)t.T[a];
+            d[a] = cg * V.dc[a] + sg * V.eu[a];
+        }
+    } else {
+        const double u = ((double)ku - (double)G.cu) * G.pu_d;
+        const double w = ((double)kv - (double)G.cv) * G.pv_d;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            p0[a] = V.S[a] - (double)t.T[a];
+            d[a] = V.sdd * V.dc[a] + u * V.eu[a] + w * V.ev[a];
+        }
+    }
+    double t0 = -INFINITY, t1 = INFINITY, dn = 0.0;
+    for (int a = 0; a < G.dim; ++a) {
+        const double lo = -0.5 * (double)t.n[a], hi = 0.5 * (double)t.n[a];
+        dn += d[a] * d[a];
+        if (d[a] == 0.0) {
+            if (!(p0[a] >= lo && p0[a] < hi)) return -1.0;
+        } else {
+            const double ta = (lo - p0[a]) / d[a], tb = (hi - p0[a]) / d[a];
+            t0 = fmax(t0, fmin(ta, tb));
+            t1 = fmin(t1, fmax(ta, tb));
+        }
+    }
+    return (t1 - t0) * sqrt(dn);
+}
+
 // Incremental Siddon walk of the line q + t d through the box over t in
 // [tin, tout] (inside the box), given inv = 1/d.  Calls f(index, length) for
 // every voxel the line crosses, in order, with the running linear index base +

@@ -39,12 +39,14 @@ struct Partition {
     int m = 0, n = 0;
     std::vector<double> PS, PT, P;  // P_S [m*n], P_T [n], P = P_S / P_T [m*n]
     std::vector<DevView> views_h;
+    std::vector<DevView64> views64_h;
     std::vector<DevVT> vt_h;        // [view * n + tile]
     std::vector<DevTile> tiles_h;
     int64_t z_floats = 0;
     int64_t max_tile_voxels = 0;
     int device = 0;
     DevView* d_views = nullptr;
+    DevView64* d_views64 = nullptr;
     DevVT* d_vt = nullptr;
     DevTile* d_tiles = nullptr;
     DevGeom dg{};

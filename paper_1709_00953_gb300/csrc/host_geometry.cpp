@@ -352,17 +352,24 @@ int partition_build(const Geometry* gp, const csgd_partition_desc* d, Partition*
 
     // ---- views (FP32, voxel units) ----
     p->views_h.resize(g.n_views);
+    p->views64_h.resize(g.n_views);
     for (int v = 0; v < g.n_views; ++v) {
         const Frame& f = g.frames[v];
         DevView& dv = p->views_h[v];
+        DevView64& d64 = p->views64_h[v];
         memset(&dv, 0, sizeof(dv));
         for (int a = 0; a < 3; ++a) {
-            dv.S[a] = (float)(f.S[a] / g.h);
+            d64.S[a] = f.S[a] / g.h;
+            d64.dc[a] = f.dc[a];
+            d64.eu[a] = f.eu[a];
+            d64.ev[a] = f.ev[a];
+            dv.S[a] = (float)d64.S[a];
             dv.dc[a] = (float)f.dc[a];
             dv.eu[a] = (float)f.eu[a];
             dv.ev[a] = (float)f.ev[a];
         }
-        dv.sdd = (float)(f.sdd / g.h);
+        d64.sdd = f.sdd / g.h;
+        dv.sdd = (float)d64.sdd;
     }
 
     // ---- per (view, tile): shadow, P tables, ray constants ----
@@ -537,6 +544,8 @@ int partition_build(const Geometry* gp, const csgd_partition_desc* d, Partition*
     dg.n_tiles = p->n;
     dg.pu = (float)pu_v;
     dg.pv = (float)pv_v;
+    dg.pu_d = pu_v;
+    dg.pv_d = pv_v;
     dg.cu = (float)cu;
     dg.cv = (float)cv;
     dg.inv_pu = (float)(1.0 / pu_v);

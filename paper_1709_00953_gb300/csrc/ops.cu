@@ -104,7 +104,9 @@ __device__ __forceinline__ void forward_single(const DevGeom& G, const WorkItem*
         int base = (t.lo[2] * G.ny + t.lo[1]) * G.nx + t.lo[0];
         Box b = tile_box(t, DIM, base, G.nx, G.nx * G.ny);
         float tin, tout;
-        if (clip<DIM>(q, inv, b, &tin, &tout)) {
+        bool sliver;
+        if (clip_sliver<DIM>(q, inv, b, &tin, &tout, &sliver) &&
+            !(sliver && exact_chord(G, it.view, ku, kv, t) <= kTouchChord)) {
             float dt = (tout - tin) * (1.0f / L);
             float t0 = sub == 0 ? tin : fmaf((float)sub, dt, tin);
             float t1 = sub == L - 1 ? tout : fmaf((float)(sub + 1), dt, tin);
@@ -131,9 +133,6 @@ __global__ void __launch_bounds__(kFwdThreads) k_project_inline(
     float* __restrict__ out, int accumulate) {
     forward_single<DIM, L>(G, it.items, it.step, x, out, accumulate);
 }
-
-// (2^-12)^2: the smallest squared gain ||A g||^2 / (h^2 ||g||^2) of a step
-constexpr double kMinGain2 = 5.9604644775390625e-08;
 
 // p = A x_J and q = A g_J for every ray of a slot in one walk (z = p + mu q by
 // linearity), with ||q||^2.  Rays come from the batch's ray table (set up once
@@ -247,11 +246,8 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     const double qs = block_sum(tq.value(), s_q);
     const double gs = block_sum(tg.value(), s_q);
     if (threadIdx.x == 0) {
-        // the exact line search; skipped (mu = 0) when ||A g|| < 2^-12 h ||g||:
-        // support that small is rounding noise (a line through a tile corner),
-        // on which gs / qs ~ 1 / length^2 would throw x_J off
-        const double floor2 = kMinGain2 * (double)G.h * (double)G.h * gs;
-        double mu = qs > floor2 ? sd.beta * gs / qs : 0.0;
+        // the exact line search (Eq. 'step'); mu = 0 when A g = 0
+        double mu = qs > 0.0 ? sd.beta * gs / qs : 0.0;
         a.sb.mu[slot] = mu;
         // non-zeros of the step, counted by the backprojection
         unsigned long long nzs = atomicExch(a.sb.nnz_slot + slot, 0ull);
@@ -284,11 +280,11 @@ struct TableArgs {
     unsigned* rmax;      // [slot] max |r| bits (scatter backprojection), or null
 };
 
-// Line of bin (ku, kv) of the item in tile-centred coordinates: q and 1/d.
+// Line of bin (ku, kv) of view `view` in tile-centred coordinates: q and 1/d.
 template <int DIM>
-__device__ __forceinline__ void table_ray(const DevGeom& G, const DevView& V, const DevVT& E,
-                                          const DevTile& tile, int ku, int kv, float q[3],
-                                          float inv[3]) {
+__device__ __forceinline__ void table_ray(const DevGeom& G, int view, const DevView& V,
+                                          const DevVT& E, const DevTile& tile, int ku, int kv,
+                                          float q[3], float inv[3]) {
     float d[3];
     ray_setup(G, V, E, ku, kv, q, d);
     reciprocal(d, inv);
@@ -303,6 +299,13 @@ __device__ __forceinline__ void table_ray(const DevGeom& G, const DevView& V, co
             if (q[ax] == face) q[ax] = nextafterf(q[ax], INFINITY);
         }
     }
+    // a line that only touches the tile (see exact_chord) gets no support in it
+    const Box b = tile_box(tile, DIM, 0, tile.n[0], tile.n[0] * tile.n[1]);
+    float tin, tout;
+    bool sliver;
+    if (clip_sliver<DIM>(q, inv, b, &tin, &tout, &sliver) && sliver &&
+        exact_chord(G, view, ku, kv, tile) <= kTouchChord)
+        q[0] = kNoSupport;
 }
 
 // The first kTablePre rays of a thread are set up before waiting for the
@@ -325,7 +328,8 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
 #pragma unroll
     for (int p = 0; p < kTablePre; ++p) {
         const int k = k0 + p * stride;
-        if (k < nr) table_ray<DIM>(G, V, E, tile, it.u0 + k % wu, it.v0 + k / wu, pq[p], pi[p]);
+        if (k < nr)
+            table_ray<DIM>(G, it.view, V, E, tile, it.u0 + k % wu, it.v0 + k / wu, pq[p], pi[p]);
     }
     pdl_wait();  // r and the table buffer belong to earlier kernels until here
     float rm = 0.f;  // max |r| of this thread's rays
@@ -345,7 +349,7 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
         const int ku = it.u0 + k % wu;
         const int kv = it.v0 + k / wu;
         float q[3], inv[3];
-        table_ray<DIM>(G, V, E, tile, ku, kv, q, inv);
+        table_ray<DIM>(G, it.view, V, E, tile, ku, kv, q, inv);
         const int64_t ray = ray_index(G, it.view, ku, kv);
         const float rv = __ldg(a.r + ray);
         rm = fmaxf(rm, fabsf(rv));
