@@ -2,16 +2,22 @@
 
 One bench step = one complete solve of the workload (solver state reset to
 x = 0, z = 0, r = y, then every block step of the workload, its residual
-refreshes and epoch averages).  The default workload is the 2D fan-beam scan
-(512^2 pixels, 720 views x 768 curved bins, 8 view blocks x 4 x 4 tiles,
-density-weighted block choice, 200 block steps).
+refreshes and epoch averages).  The default workload is the paper-scale 3D
+cone beam (256^3 voxels, 360 views x 384^2 pixels, 360 single-view row blocks
+x 4 x 4 x 4 tiles, groups of 30 views drawn by density: one epoch = 768 group
+steps, Alg. 4).
 
 metric: ray-voxel updates/s, where one update applies one non-zero A_ij of the
 block to one vector: every step does one backprojection and two forward
 products, so updates = 3 * nnz(A_{I_g}^J), counted by the kernels.
 
+roofline: the dominant kernel's algorithmic bytes (what the method itself must
+move for it, per step: backprojection r in on the step's rays R and g out on
+the tile's voxels |J|, 4 (R + |J|) bytes; dual forward x_J and g_J in, p and q
+out, 4 (2 |J| + 2 R) bytes) per second, against the measured HBM copy rate.
+
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                        [--workload fan2d_512|cone3d_256|parallel2d_64]
+                        [--workload cone3d_256|fan2d_512|parallel2d_64|batch_fan64|serve]
 """
 from __future__ import annotations
 
@@ -33,25 +39,36 @@ import numpy as np  # noqa: E402
 from synth import configs as C  # noqa: E402
 from synth import data as D  # noqa: E402
 
-# Roofline of the operators (issue-bound, not HBM-bound): ray-voxel updates per
-# non-zero of A_{I_g}^J for each timed kernel, and the instructions one update
-# costs in an incremental Siddon step (choose the axis, clip to the segment,
-# length, clamp, advance index and plane, next crossing (2), gather, multiply-
-# add): the ceiling is SMs x 128 FP32 lanes x SM clock / 10 updates per second.
+# Ray-voxel updates per non-zero of A_{I_g}^J for each timed kernel.
 UPDATES_PER_NNZ = {"backproject": 1, "forward_dual": 2}
-INSTR_PER_UPDATE = 10
-FP32_LANES_PER_SM = 128
-# enough solves for a timed region of about 1.5 s (several clock samples)
-DEFAULT_STEPS = {"fan2d_512": 250, "parallel2d_64": 250, "cone3d_256": 12, "batch_fan64": 20}
+# enough solves for a timed region of about 1 s (several clock samples)
+DEFAULT_STEPS = {"fan2d_512": 250, "parallel2d_64": 250, "cone3d_256": 16, "batch_fan64": 20}
+DEFAULT_WORKLOAD = "cone3d_256"
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of
-# the fan2d_512 workload (profiles/fan2d_512_kernels_ncu.md), valid only for the
-# kernel sources they were taken from (hash of ops.cu, device.cuh, common.h);
-# "backproject" is the ray table plus the gather, the unit the bench times.
-NCU_TRAFFIC = {
-    ("fan2d_512_720x768_8x16_importance", "1d8614d2283f6cae"): {
-        "backproject": 2106880 + 434176, "forward_dual": 2529280},
-}
+
+def algorithmic_bytes(kernel: str, rays: int, tile_voxels: int) -> int:
+    """Bytes a kernel unit must move by the method's own definition, for steps
+    covering `rays` rays of their row blocks (in tile J's shadow) and
+    `tile_voxels` voxels of their tiles (FP32): the backprojection reads r and
+    writes g; the dual forward reads x_J and g_J and writes p and q; the
+    epilogue reads p, q, z and r, writes z and r, and reads g and updates x^."""
+    if kernel == "backproject":
+        return 4 * (rays + tile_voxels)
+    if kernel == "forward_dual":
+        return 4 * (2 * rays + 2 * tile_voxels)
+    if kernel == "epilogue":
+        return 4 * (6 * rays + 3 * tile_voxels)
+    return 0
+
+
+# Per launch of a kernel unit, from one ncu capture of the workload with the
+# kernel sources of the given hash (ops.cu, device.cuh, common.h without
+# comments): dram__bytes_read.sum + dram__bytes_write.sum ("traffic") and
+# sm__instruction_throughput (the issue slots used, % of peak).  A kernel
+# edit changes the hash and voids the entry ("traffic" is then null).
+# "backproject" is the ray table plus the gather, or the ray table, the scatter
+# and its conversion pass: the unit the bench times.
+NCU_COUNTERS: dict = {}
 KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/csrc/device.cuh",
                   "paper_1709_00953_gb300/csrc/common.h")
 
@@ -75,10 +92,11 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default: 250 solves of fan2d_512, fewer for the larger workloads)")
+                    help="timed steps (default: 16 solves of cone3d_256, more for the smaller workloads)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="fan2d_512", choices=sorted(C.ALL) + ["batch_fan64", "serve"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=sorted(C.ALL) + ["batch_fan64", "serve"])
     ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second")
     ap.add_argument("--jobs", type=int, default=40, help="serve: number of requests")
     ap.add_argument("--no-e2e", action="store_true")
@@ -167,58 +185,80 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
-def oracle_sample(cfg, y, seconds: float, max_steps: int | None = None):
-    """Time the oracle's block steps (Alg. 1 inside Alg. 2-4) for about `seconds`."""
-    from oracle import siddon
-    from oracle.blocks import Partition as OPart, block_nnz
-    from oracle.geometry import Geometry as OGeom
-    from oracle.solver import OracleSolver
-    og = OGeom(**cfg["geom"])
-    op = OPart(og, cfg["part"]["tiles"], cfg["part"]["view_blocks"], cfg["part"]["det_blocks"])
-    o = OracleSolver(op, cfg["solver"], y.astype(np.float64))
-    o._new_epoch()
-    spent, steps, nnz = 0.0, 0, 0
-    while o.queue and (max_steps is None or steps < max_steps):
-        j, grp, _ = o.queue.pop(0)
+class OracleSteps:
+    """The FP64 oracle's block steps of a workload's schedule, one at a time.
+
+    A step is one Alg. 1 step of the schedule.  For grouped workloads (Alg. 4,
+    a group of s row blocks per step) one oracle step of a full group takes
+    tens of seconds on the host, so there a step is the Alg. 1 step on one row
+    block of the scheduled group (the group's blocks in turn): a bounded
+    sample with the same per-update work."""
+
+    def __init__(self, cfg, y):
+        from oracle.blocks import Partition as OPart
+        from oracle.geometry import Geometry as OGeom
+        from oracle.solver import OracleSolver
+        og = OGeom(**cfg["geom"])
+        self.op = OPart(og, cfg["part"]["tiles"], cfg["part"]["view_blocks"],
+                        cfg["part"]["det_blocks"])
+        self.o = OracleSolver(self.op, cfg["solver"], np.asarray(y, np.float64))
+        self.grouped = int(cfg["solver"].get("group_size", 1)) > 1
+        self.pending = []
+
+    def next(self):
+        if not self.pending:
+            if not self.o.queue:
+                self.o._new_epoch()
+            j, grp, _ = self.o.queue.pop(0)
+            self.pending = [(j, [i]) for i in grp] if self.grouped else [(j, list(grp))]
+        return self.pending.pop(0)
+
+    def step(self):
+        """One step: (seconds, non-zeros of its block)."""
+        from oracle.blocks import block_nnz
+        j, grp = self.next()
         t0 = time.perf_counter()
-        o.step(j, grp)
-        spent += time.perf_counter() - t0
-        nnz += block_nnz(op, grp, j)
+        self.o.step(j, grp)
+        dt = time.perf_counter() - t0
+        return dt, block_nnz(self.op, grp, j)
+
+    def what(self) -> str:
+        return ("Alg. 1 steps on single row blocks of the scheduled groups" if self.grouped
+                else "scheduled block steps (Alg. 1)")
+
+
+def oracle_sample(cfg, y, seconds: float, max_steps: int | None = None):
+    """Time the oracle's steps (see OracleSteps) for about `seconds`."""
+    from oracle import siddon
+    st = OracleSteps(cfg, y)
+    spent, steps, nnz = 0.0, 0, 0
+    while max_steps is None or steps < max_steps:
+        dt, nz = st.step()
+        spent += dt
+        nnz += nz
         steps += 1
         if spent >= seconds:
             break
-    return dict(seconds=spent, steps=steps, nnz=nnz, cores=siddon.num_threads())
+    return dict(seconds=spent, steps=steps, nnz=nnz, cores=siddon.num_threads(), what=st.what())
 
 
 def run_reference(args, cfg, world, rank):
     """--impl reference: the FP64 oracle, on the host cores, on this workload."""
     if rank != 0:
         return 0
-    y, _ = D.make_data(cfg)
-    # every step is one oracle block step: W warm-up steps, then K timed ones
-    from oracle.blocks import Partition as OPart, block_nnz
-    from oracle.geometry import Geometry as OGeom
-    from oracle.solver import OracleSolver
-    og = OGeom(**cfg["geom"])
-    op = OPart(og, cfg["part"]["tiles"], cfg["part"]["view_blocks"], cfg["part"]["det_blocks"])
-    o = OracleSolver(op, cfg["solver"], y.astype(np.float64))
-    o._new_epoch()
+    big = cfg["geom"]["kind"] == "cone3d"
+    y, _ = D.make_data(cfg, device="cuda" if big and _cuda_ok() else None)
+    st = OracleSteps(cfg, y)
     for _ in range(args.warmup):
-        if not o.queue:
-            o._new_epoch()
-        j, grp, _ = o.queue.pop(0)
-        o.step(j, grp)
+        st.step()
     t = 0.0
     nnz = 0
     for _ in range(args.steps):
-        if not o.queue:
-            o._new_epoch()
-        j, grp, _ = o.queue.pop(0)
-        t0 = time.perf_counter()
-        o.step(j, grp)
-        t += time.perf_counter() - t0
-        nnz += block_nnz(op, grp, j)
+        dt, nz = st.step()
+        t += dt
+        nnz += nz
     from oracle import siddon
+    og = st.op.geom
     value = 3.0 * nnz / t
     line = {
         "impl": "reference", "metric": "ray-voxel updates/s", "value": value,
@@ -228,17 +268,25 @@ def run_reference(args, cfg, world, rank):
         "config": {"workload": cfg["name"], "block_steps_per_solve": int(cfg["steps"]),
                    "n_rays": int(og.n_rays), "n_voxels": int(og.grid.size),
                    "parallelism": "host cores (FP64 oracle)",
-                   "step": "one block step (Alg. 1) of the workload's schedule, a bounded "
-                           "sample of its solve"},
+                   "step": "one %s, a bounded sample of the workload's solve"
+                           % st.what().replace("steps", "step", 1)},
         "cpu_baseline": {"value": value, "unit": "updates/s", "cores": siddon.num_threads(),
                          "kind": "oracle",
-                         "sample": "%d block steps of %s after %d warm-up steps"
-                                   % (args.steps, cfg["name"], args.warmup)},
+                         "sample": "%d %s of %s after %d warm-up steps"
+                                   % (args.steps, st.what(), cfg["name"], args.warmup)},
         "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
+
+
+def _cuda_ok() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
 
 
 # ---------------------------------------------------------------------------
@@ -381,30 +429,43 @@ def run_gpu(args, cfg, world, rank, local):
         return 0
 
     # ---- roofline of the dominant kernel ----
+    # algorithmic bytes (see algorithmic_bytes) of the kernel over the timed
+    # solves, per launch, against the measured HBM copy rate
     kern = {k: v for k, v in prof.items() if v["launches"] > 0}
     total_ms = sum(v["ms"] for v in kern.values())
     dom = max(("backproject", "forward_dual"), key=lambda k: kern.get(k, {"ms": 0})["ms"])
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    mhz = ck["sm_mhz"] if ck else measured_peaks().get("clocks_under_load", {}).get("sm_mhz_median", 1507.0)
-    peak = sm_count * FP32_LANES_PER_SM * mhz * 1e6 / INSTR_PER_UPDATE / 1e9
     dom_s = kern[dom]["ms"] / 1e3
+    n_launch = int(kern[dom]["launches"])
     nnz_total = nnz_per_solve * args.steps
-    achieved = UPDATES_PER_NNZ[dom] * nnz_total / dom_s / 1e9
-    traffic = NCU_TRAFFIC.get((cfg["name"], kernel_hash()), {}).get(dom)
-    hbm = measured_peaks().get("hbm_gbs")
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-            "unit": "Gupdates/s", "frac": achieved / peak, "traffic": traffic,
-            "peak_basis": "issue ceiling: %d SMs x %d FP32 lanes x %.0f MHz (median SM clock of this "
-                          "run) / %d instructions per ray-voxel update"
-                          % (sm_count, FP32_LANES_PER_SM, mhz, INSTR_PER_UPDATE),
-            "kernel_launches": int(kern[dom]["launches"]),
+    alg_launch = algorithmic_bytes(dom, rep["rays"], rep["tile_voxels"]) * args.steps / n_launch
+    achieved = alg_launch * n_launch / dom_s / 1e9
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    basis = "measured HBM copy rate (MEASURED_PEAKS.json hbm_gbs)"
+    if not hbm:
+        hbm, basis = 6800.0, "fallback HBM figure (no measured peaks file)"
+    counters = NCU_COUNTERS.get((cfg["name"], kernel_hash()), {}).get(dom, {})
+    traffic = counters.get("traffic")
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": traffic, "peak_basis": basis,
+            "algorithmic_bytes_per_launch": alg_launch, "kernel_launches": n_launch,
+            "ms_per_launch": kern[dom]["ms"] / n_launch,
+            "algorithmic_bytes_basis": "per step: backprojection 4 (R + |J|), dual forward "
+                                       "4 (2 R + 2 |J|) (R rays of the step's row blocks in "
+                                       "tile J's shadow, |J| voxels of the tile)",
+            "updates_per_s": UPDATES_PER_NNZ[dom] * nnz_total / dom_s,
             "csr_equivalent_gbs": 8.0 * nnz_total / dom_s / 1e9,
             "csr_equivalent_note": "avoided work: the bytes a stored-matrix SpMV (FP32 value + int32 "
                                    "index per non-zero) would stream for the same non-zeros"}
     if traffic is not None:
-        roof["dram_gbs"] = traffic * kern[dom]["launches"] / dom_s / 1e9
-        if hbm:
-            roof["dram_frac_of_measured_hbm"] = roof["dram_gbs"] / hbm
+        roof["dram_gbs"] = traffic * n_launch / dom_s / 1e9
+        roof["dram_frac"] = roof["dram_gbs"] / hbm
+        roof["traffic_over_algorithmic"] = traffic / alg_launch
+    if counters.get("issue_active_pct") is not None:
+        roof["issue_active_pct"] = counters["issue_active_pct"]
+    # the whole step against the same roof: SURVEY-style bytes 4 (2 R + 3 |J|) per step
+    step_bytes = 4 * (2 * rep["rays"] + 3 * rep["tile_voxels"]) * args.steps
+    roof["step_bytes_gbs"] = step_bytes / (ms / 1e3) / 1e9
     # per batch: ray table + backprojection, dual forward, epilogue; per epoch close:
     # averaging (+ pending-residual apply under epoch sync)
     close_kernels = 2 if cfg["solver"].get("sync", 0) == 1 else 1
@@ -419,8 +480,8 @@ def run_gpu(args, cfg, world, rank, local):
         cpu = {"value": 3.0 * res["nnz"] / res["seconds"], "unit": "updates/s",
                "cores": res["cores"], "kind": "oracle",
                "steps_per_s": res["steps"] / res["seconds"],
-               "sample": "first %d block steps of %s (%.1f s of FP64 oracle work)"
-                         % (res["steps"], cfg["name"], res["seconds"])}
+               "sample": "first %d %s of %s (%.1f s of FP64 oracle work)"
+                         % (res["steps"], res["what"], cfg["name"], res["seconds"])}
         # the same oracle on one host core, a shorter sample (skipped where one
         # block step alone would take too long on one core)
         from oracle import siddon
@@ -432,10 +493,10 @@ def run_gpu(args, cfg, world, rank, local):
             finally:
                 siddon.set_threads(n_all)
             cpu["value_1core"] = 3.0 * one["nnz"] / one["seconds"]
-            cpu["sample_1core"] = "first %d block steps (%.1f s)" % (one["steps"], one["seconds"])
+            cpu["sample_1core"] = "first %d %s (%.1f s)" % (one["steps"], one["what"], one["seconds"])
         else:
             cpu["value_1core"] = None
-            cpu["sample_1core"] = "skipped: one block step exceeds the sample budget on one core"
+            cpu["sample_1core"] = "skipped: one step exceeds the sample budget on one core"
 
     line = {
         "metric": "ray-voxel updates/s", "value": value, "unit": "updates/s", "n_gpus": world,

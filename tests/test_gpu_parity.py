@@ -32,6 +32,8 @@ from oracle.solver import OracleSolver  # noqa: E402
 from synth import configs as C  # noqa: E402
 from synth import data as D  # noqa: E402
 
+from parity_report import record  # noqa: E402
+
 TAU_GEOM = 2.0 ** -14
 TAU_BP = 2.0 ** -12
 REL = 1e-5
@@ -124,6 +126,7 @@ def test_project_block_parity(csgd, name):
         err = np.abs(got[rows] - ref)
         tol = REL * _abs_forward(op, grp, j, x) + TAU_GEOM * g.h * np.abs(x).max()
         assert np.all(err <= tol), (name, grp, j, float((err / tol).max()))
+        record(name, "project_block", got[rows], ref, group=list(map(int, grp)), j=int(j))
         seen = max(seen, ref.max())
     assert seen > 0
 
@@ -163,6 +166,7 @@ def test_backproject_block_parity(csgd, name):
         err = np.abs(got[vox] - ref[vox])
         tol = REL * _abs_back(op, grp, j, r[rows])[vox] + TAU_BP * g.h * np.abs(r).max()
         assert np.all(err <= tol), (name, grp, j, float((err / tol).max()))
+        record(name, "backproject_block", got[vox], ref[vox], group=list(map(int, grp)), j=int(j))
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -215,6 +219,7 @@ def test_solver_parity(csgd, name, steps):
     beta_o = np.array([l["beta"] for l in o.log])
     np.testing.assert_allclose(beta_g, beta_o, rtol=1e-12)
     np.testing.assert_allclose(mu_g, mu_o, rtol=REL, atol=1e-12)
+    record(name, "solver_mu", mu_g, mu_o, steps=steps)
     rmse = float(np.sqrt(np.mean((x_gpu - x_ref) ** 2)))
     assert rmse <= 1e-4, rmse
     assert np.abs(x_ref).max() > 0

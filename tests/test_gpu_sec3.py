@@ -69,10 +69,15 @@ def test_trends_of_sec3(X, problem):
 
 def test_group_size_one_all_blocks_matches_oracle(X, problem):
     """alpha = 1 with group size 1 draws every row block with P(I,J) > 0,
-    including sub-areas that meet the tile only at a corner of its shadow.  On
-    those the rounded geometry can leave a length of order 1e-6 h where the exact
-    one has none; the step must be skipped there as in the oracle, not taken
-    with mu ~ 1 / length^2."""
+    including detector sub-areas that meet a tile's shadow only at its edge.
+    With 187 bins the centre bin's line passes exactly through the image centre,
+    a corner of all four tiles: in exact geometry it touches those tiles in a
+    point and gives such a block no support (A g = 0, so mu = 0 by Eq. 'step').
+    The GPU must find the same (its FP32 line clips a rounding-level sliver
+    there, which the FP64 check of exact_chord removes), and follow the
+    oracle's literal run step by step for one epoch: mu to 1e-5 where the
+    block's gain ||A g|| / ||g|| is of order h, the reconstruction to RMSE
+    1e-4."""
     from oracle.blocks import Partition as OPart, project_block
     from oracle.geometry import Geometry as OGeom
     from oracle.solver import OracleSolver
@@ -104,7 +109,20 @@ def test_group_size_one_all_blocks_matches_oracle(X, problem):
     assert np.count_nonzero(ok) > 0.75 * len(ok)
     np.testing.assert_allclose(mu_g[ok], mu_o[ok], rtol=1e-5, atol=0.0)
     np.testing.assert_allclose(mu_g, mu_o, rtol=1e-2, atol=0.0)
+    from parity_report import record
+    record("sec3_group1_alpha1", "solver_mu", mu_g, mu_o, steps=int(o.steps),
+           frac_gain_ok=float(np.mean(ok)))
     assert float(np.sqrt(np.mean((x.cpu().numpy() - xo) ** 2))) <= 1e-4
+
+
+def test_group_size_one_all_blocks_converges(X, problem):
+    """The run of the test above for 10 epochs: it converges (SNR and observation
+    gap rise, nothing blows up), as the oracle does."""
+    r = problem.run(b=70.0, alpha=1.0, group_size=1, eff_epochs=10)
+    snr, gap = np.array(r["snr_db"]), np.array(r["gap_db"])
+    assert np.all(np.isfinite(snr)) and np.all(np.isfinite(gap))
+    assert np.all(np.diff(snr) > 0), snr
+    assert snr[-1] > snr[0] + 3.0 and gap[-1] > gap[0] + 6.0, (snr, gap)
 
 
 def test_sampling_trends_of_sec3d(X, problem):
