@@ -23,6 +23,7 @@ KINDS = {"parallel2d": 0, "fan2d_flat": 1, "fan2d_curved": 2, "cone3d": 3, "cust
 SEQUENTIAL, UNIFORM, IMPORTANCE, MIXED = 0, 1, 2, 3
 SYNC_COLUMN, SYNC_EPOCH = 0, 1
 SCATTER = -1  # bp_groups value of the ray-driven scatter backprojection
+BRICK = -2    # bp_groups value of the brick backprojection (no ray table)
 
 
 class CsgdError(RuntimeError):
@@ -422,14 +423,15 @@ class Solver:
 
     def set_launch(self, bp_groups: int = 0, fwd_lanes: int = 0):
         """Launch shapes of the kernels (0 = the library's models): view groups
-        per gather CTA 1..8, or SCATTER (-1) for the ray-driven backprojection;
-        lanes per ray 1, 2 or 4."""
+        per gather CTA 1..8, SCATTER (-1) for the ray-driven backprojection with
+        global atomics, or BRICK (-2) for the brick backprojection; lanes per
+        ray 1, 2 or 4."""
         _check(load().csgd_solver_set_launch(self.handle, int(bp_groups), int(fwd_lanes)))
 
     def autotune(self, trial_steps: int, stream=None) -> tuple:
         """Times every launch shape over the first trial_steps steps, keeps the
         fastest and resets the solver; returns (bp_groups, fwd_lanes), with
-        bp_groups = SCATTER (-1) if the scatter backprojection won."""
+        bp_groups = SCATTER (-1) or BRICK (-2) if one of those backprojections won."""
         c, l = ctypes.c_int32(), ctypes.c_int32()
         _check(load().csgd_solver_autotune(self.handle, int(trial_steps), ctypes.byref(c),
                                            ctypes.byref(l), _stream(stream)))

@@ -54,6 +54,34 @@ __device__ __forceinline__ Box tile_box(const DevTile& t, int dim, int base, int
     return b;
 }
 
+// Line of bin (ku, kv) of view `view` in tile-centred coordinates: q and 1/d.
+template <int DIM>
+__device__ __forceinline__ void table_ray(const DevGeom& G, int view, const DevView& V,
+                                          const DevVT& E, const DevTile& tile, int ku, int kv,
+                                          float q[3], float inv[3]) {
+    float d[3];
+    ray_setup(G, V, E, ku, kv, q, d);
+    reciprocal(d, inv);
+    // A ray parallel to axis ax whose q_ax lies exactly on a voxel face moves
+    // one ulp up: it meets the same voxels (a face belongs to the voxel above
+    // it, for the walk as for the oracle) and (face - q_ax) / d_ax is never 0 / 0.
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+        if (isinf(inv[ax])) {
+            const float hn = 0.5f * (float)tile.n[ax];
+            const float face = (float)__float2int_rn(q[ax] + hn) - hn;
+            if (q[ax] == face) q[ax] = nextafterf(q[ax], INFINITY);
+        }
+    }
+    // a line that only touches the tile (see exact_chord) gets no support in it
+    const Box b = tile_box(tile, DIM, 0, tile.n[0], tile.n[0] * tile.n[1]);
+    float tin, tout;
+    bool sliver;
+    if (clip_sliver<DIM>(q, inv, b, &tin, &tout, &sliver) && sliver &&
+        exact_chord(G, view, ku, kv, tile) <= kTouchChord)
+        q[0] = kNoSupport;
+}
+
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
@@ -140,7 +168,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_project_inline(
 // writes its partial sum of squares (FP32); the last CTA of the slot to finish
 // adds them in a fixed order (exactly as FP32 pairs, then in FP64) and computes
 // mu = beta g^T g / q^T q (no grid barrier).
-template <int DIM, int L>
+template <int DIM, int L, bool TABLE>
 __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     pdl_trigger();
     const DevGeom& G = a.G;
@@ -159,12 +187,29 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     float pp = 0.f, qp = 0.f;
     int ray = 0;
     if (active) {
-        const RayRec* rp = a.sb.table + (int64_t)slot * a.sb.table_stride + k;
-        const float4 ra = *reinterpret_cast<const float4*>(rp->a);
-        const float4 rb = *reinterpret_cast<const float4*>(rp->b);
-        ray = __float_as_int(rb.w);
-        const float q[3] = {ra.x, ra.y, rb.y};
-        const float inv[3] = {ra.z, ra.w, rb.z};
+        float q[3], inv[3];
+        if constexpr (TABLE) {
+            const RayRec* rp = a.sb.table + (int64_t)slot * a.sb.table_stride + k;
+            const float4 ra = *reinterpret_cast<const float4*>(rp->a);
+            const float4 rb = *reinterpret_cast<const float4*>(rp->b);
+            ray = __float_as_int(rb.w);
+            q[0] = ra.x;
+            q[1] = ra.y;
+            q[2] = rb.y;
+            inv[0] = ra.z;
+            inv[1] = ra.w;
+            inv[2] = rb.z;
+        } else {
+            // the line set up here, as the brick backprojection sets it up
+            const int w = find_item(a.items, sd.w0, sd.w1, k);
+            const WorkItem it = a.items[w];
+            const int within = (int)(k - it.ray_off);
+            const int wu = it.u1 - it.u0;
+            const int ku = it.u0 + within % wu, kv = it.v0 + within / wu;
+            table_ray<DIM>(G, it.view, G.views[it.view], G.vt[(int64_t)it.view * G.n_tiles + sd.j],
+                           t, ku, kv, q, inv);
+            ray = (int)ray_index(G, it.view, ku, kv);
+        }
         Box b = tile_box(t, DIM, 0, t.n[0], t.n[0] * t.n[1]);
         float tin, tout;
         if (clip<DIM>(q, inv, b, &tin, &tout)) {
@@ -279,34 +324,6 @@ struct TableArgs {
     int64_t slot_stride;
     unsigned* rmax;      // [slot] max |r| bits (scatter backprojection), or null
 };
-
-// Line of bin (ku, kv) of view `view` in tile-centred coordinates: q and 1/d.
-template <int DIM>
-__device__ __forceinline__ void table_ray(const DevGeom& G, int view, const DevView& V,
-                                          const DevVT& E, const DevTile& tile, int ku, int kv,
-                                          float q[3], float inv[3]) {
-    float d[3];
-    ray_setup(G, V, E, ku, kv, q, d);
-    reciprocal(d, inv);
-    // A ray parallel to axis ax whose q_ax lies exactly on a voxel face moves
-    // one ulp up: it meets the same voxels (a face belongs to the voxel above
-    // it, for the walk as for the oracle) and (face - q_ax) / d_ax is never 0 / 0.
-#pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) {
-        if (isinf(inv[ax])) {
-            const float hn = 0.5f * (float)tile.n[ax];
-            const float face = (float)__float2int_rn(q[ax] + hn) - hn;
-            if (q[ax] == face) q[ax] = nextafterf(q[ax], INFINITY);
-        }
-    }
-    // a line that only touches the tile (see exact_chord) gets no support in it
-    const Box b = tile_box(tile, DIM, 0, tile.n[0], tile.n[0] * tile.n[1]);
-    float tin, tout;
-    bool sliver;
-    if (clip_sliver<DIM>(q, inv, b, &tin, &tout, &sliver) && sliver &&
-        exact_chord(G, view, ku, kv, tile) <= kTouchChord)
-        q[0] = kNoSupport;
-}
 
 // The first kTablePre rays of a thread are set up before waiting for the
 // previous kernel (they need only the geometry); the residual is read and the
@@ -961,6 +978,284 @@ __global__ void __launch_bounds__(kConvThreads) k_scatter_convert(const ScatterA
 }
 
 // ---------------------------------------------------------------------------
+// Backprojection by bricks.  A CTA owns one brick of the tile (16^3 voxels in
+// 3D, 32^2 in 2D) for one slot and sums len * r over the slot's lines that
+// cross it, in shared memory.  For every view of the slot it takes the bins of
+// the work item whose centre lines can cross the brick (the bounding rectangle
+// of the projections of the brick's corners, i.e. of its shadow), sets each
+// line up exactly as the dual forward does (table_ray: the same q and 1/d, the
+// same treatment of lines that only touch the tile), clips it to the brick and
+// walks it there.  Plane crossings are the forward's, so every (line, voxel)
+// length is the forward's, and each such pair lies in exactly one brick.
+// Terms round(2^S len r) go to 32-bit fixed-point sums with shared-memory
+// integer atomics: the sums are exact and do not depend on the order of the
+// additions, so the result is deterministic.  S is chosen per CTA from the
+// largest |r| it reads and a bound on the lines one voxel can receive (per
+// view, the bins within hw_u, hw_v of the voxel's centre), so that no sum can
+// overflow.  No ray table, no global atomics, no conversion pass.
+// ---------------------------------------------------------------------------
+template <int DIM>
+struct BrickShape {
+    static constexpr int n0 = 16, n1 = 16, n2 = 16;
+};
+template <>
+struct BrickShape<2> {
+    static constexpr int n0 = 32, n1 = 32, n2 = 1;
+};
+constexpr int kBrickThreads = 256;
+constexpr int kBrickViews = 64;  // views staged in shared memory at a time
+
+struct BrickView {
+    int u0, nu;   // bins [u0, u0 + nu) x [v0, v0 + nv) of the item that can cross the brick
+    int v0, nv;
+    int start;    // (view, bin) pairs of the staged views before this one
+    int view;
+    int terms;    // bound on this view's lines through one voxel
+    int pad;
+};
+
+struct BrickArgs {
+    DevGeom G;
+    const WorkItem* items;
+    const StepDesc* steps;
+    int first;
+    const float* r;
+    SolverBuffers sb;
+};
+
+inline int brick_count(const DevTile& t, int dim) {
+    const int b0 = dim == 3 ? BrickShape<3>::n0 : BrickShape<2>::n0;
+    const int b1 = dim == 3 ? BrickShape<3>::n1 : BrickShape<2>::n1;
+    const int b2 = dim == 3 ? BrickShape<3>::n2 : 1;
+    return ((t.n[0] + b0 - 1) / b0) * ((t.n[1] + b1 - 1) / b1) * ((t.n[2] + b2 - 1) / b2);
+}
+
+// Detector coordinates (bin index units: bin k's centre at w = k) of a point P
+// (grid-centred voxel units) in view V; false if P is not in front of the source.
+__device__ __forceinline__ bool det_coord(const DevGeom& G, const DevView& V, const float P[3],
+                                          float* wu, float* wv) {
+    const float bu = fmaf(0.5f, (float)G.nu, -0.5f), bv = fmaf(0.5f, (float)G.nv, -0.5f);
+    if (G.kind == PARALLEL_2D) {
+        *wu = fmaf(P[0] * V.eu[0] + P[1] * V.eu[1], G.inv_pu, bu);
+        *wv = 0.f;
+        return true;
+    }
+    float r[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r[a] = P[a] - V.S[a];
+    const float D = r[0] * V.dc[0] + r[1] * V.dc[1] + r[2] * V.dc[2];
+    if (!(D > 1e-3f)) return false;
+    const float Lu = r[0] * V.eu[0] + r[1] * V.eu[1] + r[2] * V.eu[2];
+    if (G.kind == FAN_2D_CURVED) {
+        *wu = fmaf(atan2f(Lu, D), G.inv_pu, bu);
+        *wv = 0.f;
+        return true;
+    }
+    const float iD = V.sdd / D;
+    *wu = fmaf(Lu * iD, G.inv_pu, bu);
+    const float Lv = r[0] * V.ev[0] + r[1] * V.ev[1] + r[2] * V.ev[2];
+    *wv = G.dim == 3 ? fmaf(Lv * iD, G.inv_pv, bv) : 0.f;
+    return true;
+}
+
+// Window of the item's bins whose centre lines can cross the brick [blo, bhi)
+// (grid-centred voxel units): the bounding rectangle of its corners' detector
+// coordinates, widened by kShadowMargin for rounding.
+template <int DIM>
+__device__ __forceinline__ void brick_window(const DevGeom& G, const DevView& V, const WorkItem& it,
+                                             const float blo[3], const float bhi[3],
+                                             BrickView* bv) {
+    float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    bool all = false;
+#pragma unroll
+    for (int c = 0; c < (DIM == 3 ? 8 : 4); ++c) {
+        const float P[3] = {(c & 1) ? bhi[0] : blo[0], (c & 2) ? bhi[1] : blo[1],
+                            DIM == 3 ? ((c & 4) ? bhi[2] : blo[2]) : 0.f};
+        float wu, wv;
+        if (!det_coord(G, V, P, &wu, &wv)) all = true;
+        umin = fminf(umin, wu);
+        umax = fmaxf(umax, wu);
+        vmin = fminf(vmin, wv);
+        vmax = fmaxf(vmax, wv);
+    }
+    int u0 = it.u0, u1 = it.u1, v0 = it.v0, v1 = it.v1;
+    if (!all) {
+        u0 = max(u0, __float2int_ru(fmaxf(umin - kShadowMargin, -1e9f)));
+        u1 = min(u1, __float2int_rd(fminf(umax + kShadowMargin, 1e9f)) + 1);
+        if (DIM == 3) {
+            v0 = max(v0, __float2int_ru(fmaxf(vmin - kShadowMargin, -1e9f)));
+            v1 = min(v1, __float2int_rd(fminf(vmax + kShadowMargin, 1e9f)) + 1);
+        }
+    }
+    bv->u0 = u0;
+    bv->nu = max(0, u1 - u0);
+    bv->v0 = v0;
+    bv->nv = max(0, v1 - v0);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBrickThreads) k_backproject_brick(const BrickArgs a) {
+    using BS = BrickShape<DIM>;
+    constexpr int kVox = BS::n0 * BS::n1 * BS::n2;
+    __shared__ int acc[kVox];
+    __shared__ BrickView sv[kBrickViews];
+    __shared__ DevView sview[kBrickViews];
+    __shared__ DevVT svt[kBrickViews];
+    __shared__ float s_red[kBrickThreads / 32];
+    __shared__ unsigned s_nz[kBrickThreads / 32];
+    __shared__ float s_terms;  // bound on the terms one voxel receives (all views)
+    __shared__ int s_total;
+    pdl_trigger();
+    const DevGeom& G = a.G;
+    const int slot = blockIdx.y;
+    const StepDesc sd = a.steps[a.first + slot];
+    const DevTile t = G.tiles[sd.j];
+    // this CTA's brick: voxels [b_lo, b_lo + bn) of the tile
+    const int nb0 = (t.n[0] + BS::n0 - 1) / BS::n0, nb1 = (t.n[1] + BS::n1 - 1) / BS::n1;
+    const int bidx[3] = {(int)blockIdx.x % nb0, ((int)blockIdx.x / nb0) % nb1,
+                         (int)blockIdx.x / (nb0 * nb1)};
+    const int b_lo[3] = {bidx[0] * BS::n0, bidx[1] * BS::n1, bidx[2] * BS::n2};
+    const int bn[3] = {min(BS::n0, t.n[0] - b_lo[0]), min(BS::n1, t.n[1] - b_lo[1]),
+                       DIM == 3 ? min(BS::n2, t.n[2] - b_lo[2]) : 1};
+    Box bb;
+    float blo[3], bhi[3];  // grid-centred
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        bb.lo[c] = c < DIM ? -0.5f * (float)t.n[c] + (float)b_lo[c] : -0.5f;
+        bb.n[c] = bn[c];
+        blo[c] = c < DIM ? t.T[c] + bb.lo[c] : 0.f;
+        bhi[c] = c < DIM ? blo[c] + (float)bn[c] : 0.f;
+    }
+    bb.stride[0] = 1;
+    bb.stride[1] = bn[0];
+    bb.stride[2] = bn[0] * bn[1];
+    bb.base = 0;
+    const int nvox = bn[0] * bn[1] * bn[2];
+    for (int v = threadIdx.x; v < kVox; v += blockDim.x) acc[v] = 0;
+    const int n_items = sd.w1 - sd.w0;
+    // stage views [base, base + nb): windows, frames and constants, prefix counts
+    auto stage = [&](int base, int nb) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+            const WorkItem it = a.items[sd.w0 + base + k];
+            sview[k] = G.views[it.view];
+            svt[k] = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
+            brick_window<DIM>(G, sview[k], it, blo, bhi, &sv[k]);
+            sv[k].view = it.view;
+            const int tu = (int)fminf(2.0f * svt[k].hw_u, 4096.f) + 2;
+            const int tv = DIM == 3 ? (int)fminf(2.0f * svt[k].hw_v, 4096.f) + 2 : 1;
+            sv[k].terms = tu * tv;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            float terms = 0.f;
+            for (int k = 0; k < nb; ++k) {
+                sv[k].start = run;
+                run += sv[k].nu * sv[k].nv;
+                terms += (float)sv[k].terms;
+            }
+            s_total = run;
+            s_terms += terms;
+        }
+        __syncthreads();
+    };
+    if (threadIdx.x == 0) s_terms = 0.f;
+    // pass 1: the largest |r| of the CTA's lines
+    float rm = 0.f;
+    for (int base = 0; base < n_items; base += kBrickViews) {
+        const int nb = min(kBrickViews, n_items - base);
+        stage(base, nb);
+        if (base == 0) pdl_wait();  // r is the previous kernels'
+        int vi = 0;
+        for (int k = threadIdx.x; k < s_total; k += blockDim.x) {
+            while (vi + 1 < nb && k >= sv[vi + 1].start) ++vi;
+            const BrickView& w = sv[vi];
+            const int kk = k - w.start;
+            const int ku = w.u0 + kk % w.nu, kv = w.v0 + kk / w.nu;
+            rm = fmaxf(rm, fabsf(__ldg(a.r + ray_index(G, w.view, ku, kv))));
+        }
+    }
+    if (n_items <= 0) pdl_wait();
+    {
+        const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(rm));
+        if ((threadIdx.x & 31) == 0) s_nz[threadIdx.x >> 5] = wm;
+    }
+    __syncthreads();
+    unsigned mbits = 0;
+    for (int w = 0; w < kBrickThreads / 32; ++w) mbits = max(mbits, s_nz[w]);
+    // every voxel receives at most s_terms terms, each below 2 max|r| 2^S (a unit
+    // voxel's chord is at most sqrt(3)), so sums stay below 2^30 when
+    // s_terms 2 max|r| < 2^(30 - S)
+    const float bound = __uint_as_float(mbits) * 2.0f * fmaxf(1.f, s_terms);
+    int e = 0;
+    frexpf(bound, &e);  // bound < 2^e
+    const int S = min(100, max(-100, 30 - e));
+    const float sc = pow2f(S);
+    // pass 2: walk every line through the brick
+    int nz = 0;
+    for (int base = 0; base < n_items; base += kBrickViews) {
+        const int nb = min(kBrickViews, n_items - base);
+        if (n_items > kBrickViews) stage(base, nb);
+        int vi = 0;
+        for (int k = threadIdx.x; k < s_total; k += blockDim.x) {
+            while (vi + 1 < nb && k >= sv[vi + 1].start) ++vi;
+            const BrickView& w = sv[vi];
+            const int kk = k - w.start;
+            const int ku = w.u0 + kk % w.nu, kv = w.v0 + kk / w.nu;
+            const float rs = __ldg(a.r + ray_index(G, w.view, ku, kv)) * sc;
+            float q[3], inv[3];
+            table_ray<DIM>(G, w.view, sview[vi], svt[vi], t, ku, kv, q, inv);
+            float tin, tout;
+            if (!clip<DIM>(q, inv, bb, &tin, &tout)) continue;
+            auto add = [&](const int (&id)[kFwdBatch], const float (&ln)[kFwdBatch]) {
+#pragma unroll
+                for (int u = 0; u < kFwdBatch; ++u) {
+                    if (ln[u] > 0.f && (unsigned)id[u] < (unsigned)nvox) {
+                        ++nz;  // every non-zero of the block counts, whatever r is
+                        const int term = __float2int_rn(ln[u] * rs);
+                        if (term) atomicAdd(acc + id[u], term);
+                    }
+                }
+            };
+            if constexpr (DIM == 2) walk2_batched<kFwdBatch>(q, inv, bb, tin, tout, add);
+            else walk3_batched<kFwdBatch>(q, inv, bb, tin, tout, add);
+        }
+    }
+    __syncthreads();
+    // g_J = h 2^-S sum, written as (x_J, g_J) pairs; g^T g and nnz per CTA
+    const float isc = pow2f(-S) * G.h;
+    float2* gout = reinterpret_cast<float2*>(a.sb.g) + (int64_t)slot * a.sb.g_stride;
+    const float* xt = a.sb.x + t.voff;
+    float gg = 0.f;
+    for (int v = threadIdx.x; v < nvox; v += blockDim.x) {
+        const int x0 = v % bn[0], x1 = (v / bn[0]) % bn[1], x2 = v / (bn[0] * bn[1]);
+        const int vt = ((b_lo[2] + x2) * t.n[1] + (b_lo[1] + x1)) * t.n[0] + b_lo[0] + x0;
+        const float gv = (float)acc[v] * isc;
+        gout[vt] = make_float2(xt[vt], gv);
+        gg = fmaf(gv, gv, gg);
+    }
+    const float wg = warp_sum_f(gg);
+    const unsigned wn = __reduce_add_sync(0xffffffffu, (unsigned)nz);
+    __syncthreads();  // s_nz is reused
+    if ((threadIdx.x & 31) == 0) {
+        s_red[threadIdx.x >> 5] = wg;
+        s_nz[threadIdx.x >> 5] = wn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float cg = 0.f;
+        unsigned long long cn = 0;
+        for (int w = 0; w < kBrickThreads / 32; ++w) {
+            cg += s_red[w];
+            cn += s_nz[w];
+        }
+        a.sb.gg_part[(int64_t)slot * a.sb.gg_stride + blockIdx.x] = cg;
+        if (a.sb.nnz_slot && cn) atomicAdd(a.sb.nnz_slot + slot, cn);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // epilogue, averaging, conversions
 // ---------------------------------------------------------------------------
 struct EpiArgs {
@@ -1312,13 +1607,27 @@ cudaError_t noalloc_table_address(int device, RayRec** out) {
     return cudaSuccess;
 }
 
+template <bool TABLE>
+static cudaError_t launch_forward(int dim, int L, dim3 grid, cudaStream_t s, const FwdSolverArgs& f) {
+    const dim3 block(kFwdThreads);
+    if (dim == 2) {
+        if (L == 1) return launch_pdl(k_forward_dual<2, 1, TABLE>, grid, block, s, f);
+        if (L == 2) return launch_pdl(k_forward_dual<2, 2, TABLE>, grid, block, s, f);
+        return launch_pdl(k_forward_dual<2, 4, TABLE>, grid, block, s, f);
+    }
+    if (L == 1) return launch_pdl(k_forward_dual<3, 1, TABLE>, grid, block, s, f);
+    if (L == 2) return launch_pdl(k_forward_dual<3, 2, TABLE>, grid, block, s, f);
+    return launch_pdl(k_forward_dual<3, 4, TABLE>, grid, block, s, f);
+}
+
 cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* items,
                          const StepDesc* steps, const BatchLaunch& b, const SolverBuffers& sb,
                          int sm_count, cudaStream_t s, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], s);
     const bool scatter = b.bp_groups == kBPScatter;
+    const bool brick = b.bp_groups == kBPBrick;
     BPPlan plan = plan_backprojection(G, tile, b.nslots, (b.n_items + b.nslots - 1) / b.nslots,
-                                      sm_count, scatter ? 0 : b.bp_groups);
+                                      sm_count, scatter || brick ? 0 : b.bp_groups);
     const int L = b.fwd_lanes == 1 || b.fwd_lanes == 2 || b.fwd_lanes == 4
                       ? b.fwd_lanes : lanes_per_ray(b.max_rays * b.nslots, sm_count);
     int64_t nb = (b.max_rays * L + kFwdThreads - 1) / kFwdThreads;
@@ -1333,10 +1642,25 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     ta.table = sb.table;
     ta.slot_stride = sb.table_stride;
     ta.rmax = scatter ? sb.rmax : nullptr;
-    cudaError_t e = launch_table(G, b.n_items, b.max_item_rays, s, ta, nullptr, items);
+    cudaError_t e = brick ? cudaSuccess
+                          : launch_table(G, b.n_items, b.max_item_rays, s, ta, nullptr, items);
     if (e != cudaSuccess) return e;
     int n_gg = plan.blocks;
-    if (scatter) {
+    if (brick) {
+        BrickArgs ba;
+        ba.G = G;
+        ba.items = items;
+        ba.steps = steps;
+        ba.first = b.first;
+        ba.r = sb.r;
+        ba.sb = sb;
+        n_gg = brick_count(tile, G.dim);
+        if (n_gg > sb.gg_stride) return cudaErrorInvalidValue;
+        const dim3 grid((unsigned)n_gg, b.nslots);
+        e = G.dim == 2 ? launch_pdl(k_backproject_brick<2>, grid, dim3(kBrickThreads), s, ba)
+                       : launch_pdl(k_backproject_brick<3>, grid, dim3(kBrickThreads), s, ba);
+        if (e != cudaSuccess) return e;
+    } else if (scatter) {
         ScatterArgs sa;
         sa.G = G;
         sa.steps = steps;
@@ -1387,15 +1711,9 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     f.n_gg = n_gg;
     f.sb = sb;
     dim3 grid((unsigned)nb, b.nslots);
-    if (G.dim == 2) {
-        if (L == 1) e = launch_pdl(k_forward_dual<2, 1>, grid, dim3(kFwdThreads), s, f);
-        else if (L == 2) e = launch_pdl(k_forward_dual<2, 2>, grid, dim3(kFwdThreads), s, f);
-        else e = launch_pdl(k_forward_dual<2, 4>, grid, dim3(kFwdThreads), s, f);
-    } else {
-        if (L == 1) e = launch_pdl(k_forward_dual<3, 1>, grid, dim3(kFwdThreads), s, f);
-        else if (L == 2) e = launch_pdl(k_forward_dual<3, 2>, grid, dim3(kFwdThreads), s, f);
-        else e = launch_pdl(k_forward_dual<3, 4>, grid, dim3(kFwdThreads), s, f);
-    }
+    // the brick backprojection builds no ray table: the forward sets its lines up
+    if (brick) e = launch_forward<false>(G.dim, L, grid, s, f);
+    else e = launch_forward<true>(G.dim, L, grid, s, f);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], s);

@@ -26,6 +26,7 @@ constexpr int kFwdThreads = 128;  // threads of a dual-forward CTA (256 and 64 m
 constexpr int kBPVox = 64;
 constexpr int kBPMaxChunks = 8;  // view groups per CTA at most
 constexpr int kBPScatter = -1;   // bp_groups value selecting the scatter backprojection
+constexpr int kBPBrick = -2;     // bp_groups value selecting the brick backprojection
 inline int bp_patch(int dim, int axis) { return dim == 2 ? (axis < 2 ? 8 : 1) : 4; }
 inline int bp_blocks(const DevTile& t, int dim) {
     int b = 1;
@@ -103,7 +104,8 @@ struct BatchLaunch {
     int64_t max_item_rays;   // rays of the largest work item
     int sync_epoch;
     int bp_groups = 0;       // view groups per backprojection CTA (0: occupancy model;
-                             // kBPScatter: ray-driven scatter backprojection)
+                             // kBPScatter: ray-driven scatter backprojection;
+                             // kBPBrick: brick backprojection, no ray table)
     int fwd_lanes = 0;       // lanes per ray of the dual forward (0: by ray count)
 };
 
