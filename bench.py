@@ -105,8 +105,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library's launch-shape models instead of csgd_solver_autotune")
     ap.add_argument("--launch", default=None,
-                    help="fixed launch shapes, --launch=bp_groups,fwd_lanes (bp_groups -1: scatter) "
-                         "instead of csgd_solver_autotune")
+                    help="fixed launch shapes, --launch=bp_groups,fwd_lanes (bp_groups -1: scatter, "
+                         "-2: bricks) instead of csgd_solver_autotune")
     a = ap.parse_args()
     if a.steps is None:
         a.steps = DEFAULT_STEPS.get(a.workload, 20)
@@ -513,7 +513,8 @@ def run_gpu(args, cfg, world, rank, local):
         "roofline": roof, "kernels": kernels, "gpu_launches": launches,
         "launch": "one CUDA graph per solve (reset, all block steps, epoch averages)",
         "launch_shapes": ({"autotuned": not args.launch,
-                           "backprojection": "scatter" if shapes[0] == csgd.SCATTER else "gather",
+                           "backprojection": "scatter" if shapes[0] == csgd.SCATTER else (
+                               "brick" if shapes[0] in csgd.BRICKS else "gather"),
                            "view_groups": shapes[0], "lanes_per_ray": shapes[1]}
                           if shapes else {"autotuned": False}),
         "kernel_timing": "per-launch CUDA events in a second pass of the same %d solves launched "

@@ -23,7 +23,8 @@ KINDS = {"parallel2d": 0, "fan2d_flat": 1, "fan2d_curved": 2, "cone3d": 3, "cust
 SEQUENTIAL, UNIFORM, IMPORTANCE, MIXED = 0, 1, 2, 3
 SYNC_COLUMN, SYNC_EPOCH = 0, 1
 SCATTER = -1  # bp_groups value of the ray-driven scatter backprojection
-BRICK = -2    # bp_groups value of the brick backprojection (no ray table)
+BRICK = -2    # bp_groups values -2, -3, -4: the brick backprojection (no ray table)
+BRICKS = (-2, -3, -4)  # with brick shapes 0, 1, 2 (3D 16x16x{16,8,4}, 2D {32,16,8}^2)
 
 
 class CsgdError(RuntimeError):

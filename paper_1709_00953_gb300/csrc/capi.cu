@@ -1441,9 +1441,9 @@ int32_t csgd_solver_set_state(csgd_solver* S, const void* buf, int64_t size, csg
 // ---------------------------------------------------------------------------
 int32_t csgd_solver_set_launch(csgd_solver* S, int32_t bp_groups, int32_t fwd_lanes) {
     if (!S) return fail(CSGD_ERR_INVALID_ARG, "NULL solver");
-    if (bp_groups < kBPBrick || bp_groups > kBPMaxChunks)
+    if (bp_groups < kBPBrickLast || bp_groups > kBPMaxChunks)
         return fail(CSGD_ERR_INVALID_ARG,
-                    "view groups must be -2 (bricks), -1 (scatter), 0 (model) or 1..8");
+                    "view groups must be -4..-2 (bricks), -1 (scatter), 0 (model) or 1..8");
     if (fwd_lanes != 0 && fwd_lanes != 1 && fwd_lanes != 2 && fwd_lanes != 4)
         return fail(CSGD_ERR_INVALID_ARG, "lanes per ray must be 0 (model), 1, 2 or 4");
     S->bp_groups = bp_groups;
@@ -1483,8 +1483,10 @@ int32_t csgd_solver_autotune(csgd_solver* S, int64_t trial_steps, int32_t* bp_gr
     int best_c = 0;
     double best = 0.0;
     // the gather with 1..8 view groups per CTA, then the scatter, then the bricks
-    for (int c = 1; rc == CSGD_OK && c <= kBPMaxChunks + 2; ++c) {
-        S->bp_groups = c <= kBPMaxChunks ? c : (c == kBPMaxChunks + 1 ? kBPScatter : kBPBrick);
+    const int n_shapes = kBPMaxChunks + 1 + (kBPBrick - kBPBrickLast + 1);
+    for (int c = 1; rc == CSGD_OK && c <= n_shapes; ++c) {
+        S->bp_groups = c <= kBPMaxChunks ? c
+                     : (c == kBPMaxChunks + 1 ? kBPScatter : kBPBrick - (c - kBPMaxChunks - 2));
         rc = trial_ms(S, trial_steps, 0, s, &ms);
         if (rc == CSGD_OK && (best_c == 0 || ms < best)) {
             best = ms;

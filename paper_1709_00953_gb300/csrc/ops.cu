@@ -176,9 +176,6 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     const StepDesc sd = a.steps[a.first + slot];
     const DevTile t = G.tiles[sd.j];
     const int nvox = t.n[0] * t.n[1] * t.n[2];
-    pdl_wait();
-    // (x_J, g_J) interleaved per voxel by the backprojection: one 8-byte gather per voxel
-    const float2* __restrict__ xg = reinterpret_cast<const float2*>(a.sb.g) + (int64_t)slot * a.sb.g_stride;
     const int lane = threadIdx.x & 31;
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t k = gid / L;
@@ -186,8 +183,25 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     const bool active = k < sd.n_rays;
     float pp = 0.f, qp = 0.f;
     int ray = 0;
+    float q[3], inv[3];
+    if constexpr (!TABLE) {
+        // the line set up here, before the wait (it depends on the geometry
+        // only), as the brick backprojection sets it up
+        if (active) {
+            const int w = find_item(a.items, sd.w0, sd.w1, k);
+            const WorkItem it = a.items[w];
+            const int within = (int)(k - it.ray_off);
+            const int wu = it.u1 - it.u0;
+            const int ku = it.u0 + within % wu, kv = it.v0 + within / wu;
+            table_ray<DIM>(G, it.view, G.views[it.view], G.vt[(int64_t)it.view * G.n_tiles + sd.j],
+                           t, ku, kv, q, inv);
+            ray = (int)ray_index(G, it.view, ku, kv);
+        }
+    }
+    pdl_wait();
+    // (x_J, g_J) interleaved per voxel by the backprojection: one 8-byte gather per voxel
+    const float2* __restrict__ xg = reinterpret_cast<const float2*>(a.sb.g) + (int64_t)slot * a.sb.g_stride;
     if (active) {
-        float q[3], inv[3];
         if constexpr (TABLE) {
             const RayRec* rp = a.sb.table + (int64_t)slot * a.sb.table_stride + k;
             const float4 ra = *reinterpret_cast<const float4*>(rp->a);
@@ -199,16 +213,6 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
             inv[0] = ra.z;
             inv[1] = ra.w;
             inv[2] = rb.z;
-        } else {
-            // the line set up here, as the brick backprojection sets it up
-            const int w = find_item(a.items, sd.w0, sd.w1, k);
-            const WorkItem it = a.items[w];
-            const int within = (int)(k - it.ray_off);
-            const int wu = it.u1 - it.u0;
-            const int ku = it.u0 + within % wu, kv = it.v0 + within / wu;
-            table_ray<DIM>(G, it.view, G.views[it.view], G.vt[(int64_t)it.view * G.n_tiles + sd.j],
-                           t, ku, kv, q, inv);
-            ray = (int)ray_index(G, it.view, ku, kv);
         }
         Box b = tile_box(t, DIM, 0, t.n[0], t.n[0] * t.n[1]);
         float tin, tout;
@@ -994,13 +998,16 @@ __global__ void __launch_bounds__(kConvThreads) k_scatter_convert(const ScatterA
 // view, the bins within hw_u, hw_v of the voxel's centre), so that no sum can
 // overflow.  No ray table, no global atomics, no conversion pass.
 // ---------------------------------------------------------------------------
-template <int DIM>
+// Brick shapes, by dimension and shape index SH (the autotuner picks one):
+// 3D 16 x 16 x {16, 8, 4}; 2D {32, 16, 8} squared.  Thinner bricks give more
+// CTAs per slot and smaller windows, at more line set-ups per line.
+template <int DIM, int SH>
 struct BrickShape {
-    static constexpr int n0 = 16, n1 = 16, n2 = 16;
+    static constexpr int n0 = 16, n1 = 16, n2 = SH == 0 ? 16 : (SH == 1 ? 8 : 4);
 };
-template <>
-struct BrickShape<2> {
-    static constexpr int n0 = 32, n1 = 32, n2 = 1;
+template <int SH>
+struct BrickShape<2, SH> {
+    static constexpr int n0 = SH == 0 ? 32 : (SH == 1 ? 16 : 8), n1 = n0, n2 = 1;
 };
 constexpr int kBrickThreads = 256;
 constexpr int kBrickViews = 64;  // views staged in shared memory at a time
@@ -1023,11 +1030,17 @@ struct BrickArgs {
     SolverBuffers sb;
 };
 
-inline int brick_count(const DevTile& t, int dim) {
-    const int b0 = dim == 3 ? BrickShape<3>::n0 : BrickShape<2>::n0;
-    const int b1 = dim == 3 ? BrickShape<3>::n1 : BrickShape<2>::n1;
-    const int b2 = dim == 3 ? BrickShape<3>::n2 : 1;
-    return ((t.n[0] + b0 - 1) / b0) * ((t.n[1] + b1 - 1) / b1) * ((t.n[2] + b2 - 1) / b2);
+template <int DIM, int SH>
+inline int brick_count_of(const DevTile& t) {
+    using BS = BrickShape<DIM, SH>;
+    return ((t.n[0] + BS::n0 - 1) / BS::n0) * ((t.n[1] + BS::n1 - 1) / BS::n1) *
+           ((t.n[2] + BS::n2 - 1) / BS::n2);
+}
+inline int brick_count(const DevTile& t, int dim, int sh) {
+    if (dim == 2) return sh == 0 ? brick_count_of<2, 0>(t) : (sh == 1 ? brick_count_of<2, 1>(t)
+                                                                        : brick_count_of<2, 2>(t));
+    return sh == 0 ? brick_count_of<3, 0>(t) : (sh == 1 ? brick_count_of<3, 1>(t)
+                                                         : brick_count_of<3, 2>(t));
 }
 
 // Detector coordinates (bin index units: bin k's centre at w = k) of a point P
@@ -1093,9 +1106,9 @@ __device__ __forceinline__ void brick_window(const DevGeom& G, const DevView& V,
     bv->nv = max(0, v1 - v0);
 }
 
-template <int DIM>
-__global__ void __launch_bounds__(kBrickThreads) k_backproject_brick(const BrickArgs a) {
-    using BS = BrickShape<DIM>;
+template <int DIM, int SH>
+__global__ void __launch_bounds__(kBrickThreads, 4) k_backproject_brick(const BrickArgs a) {
+    using BS = BrickShape<DIM, SH>;
     constexpr int kVox = BS::n0 * BS::n1 * BS::n2;
     __shared__ int acc[kVox];
     __shared__ BrickView sv[kBrickViews];
@@ -1625,7 +1638,8 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
                          int sm_count, cudaStream_t s, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[0], s);
     const bool scatter = b.bp_groups == kBPScatter;
-    const bool brick = b.bp_groups == kBPBrick;
+    const bool brick = b.bp_groups <= kBPBrick && b.bp_groups >= kBPBrickLast;
+    const int sh = brick ? kBPBrick - b.bp_groups : 0;  // brick shape index
     BPPlan plan = plan_backprojection(G, tile, b.nslots, (b.n_items + b.nslots - 1) / b.nslots,
                                       sm_count, scatter || brick ? 0 : b.bp_groups);
     const int L = b.fwd_lanes == 1 || b.fwd_lanes == 2 || b.fwd_lanes == 4
@@ -1654,11 +1668,17 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
         ba.first = b.first;
         ba.r = sb.r;
         ba.sb = sb;
-        n_gg = brick_count(tile, G.dim);
+        n_gg = brick_count(tile, G.dim, sh);
         if (n_gg > sb.gg_stride) return cudaErrorInvalidValue;
-        const dim3 grid((unsigned)n_gg, b.nslots);
-        e = G.dim == 2 ? launch_pdl(k_backproject_brick<2>, grid, dim3(kBrickThreads), s, ba)
-                       : launch_pdl(k_backproject_brick<3>, grid, dim3(kBrickThreads), s, ba);
+        const dim3 grid((unsigned)n_gg, b.nslots), block(kBrickThreads);
+        if (G.dim == 2)
+            e = sh == 0 ? launch_pdl(k_backproject_brick<2, 0>, grid, block, s, ba)
+              : sh == 1 ? launch_pdl(k_backproject_brick<2, 1>, grid, block, s, ba)
+                        : launch_pdl(k_backproject_brick<2, 2>, grid, block, s, ba);
+        else
+            e = sh == 0 ? launch_pdl(k_backproject_brick<3, 0>, grid, block, s, ba)
+              : sh == 1 ? launch_pdl(k_backproject_brick<3, 1>, grid, block, s, ba)
+                        : launch_pdl(k_backproject_brick<3, 2>, grid, block, s, ba);
         if (e != cudaSuccess) return e;
     } else if (scatter) {
         ScatterArgs sa;

@@ -26,7 +26,8 @@ constexpr int kFwdThreads = 128;  // threads of a dual-forward CTA (256 and 64 m
 constexpr int kBPVox = 64;
 constexpr int kBPMaxChunks = 8;  // view groups per CTA at most
 constexpr int kBPScatter = -1;   // bp_groups value selecting the scatter backprojection
-constexpr int kBPBrick = -2;     // bp_groups value selecting the brick backprojection
+constexpr int kBPBrick = -2;     // bp_groups values -2, -3, -4 select the brick
+constexpr int kBPBrickLast = -4; // backprojection with brick shape 0, 1, 2
 inline int bp_patch(int dim, int axis) { return dim == 2 ? (axis < 2 ? 8 : 1) : 4; }
 inline int bp_blocks(const DevTile& t, int dim) {
     int b = 1;

@@ -259,10 +259,11 @@ def test_scatter_backprojection_parity(csgd, name, steps, lanes):
     np.testing.assert_array_equal(x_gpu, x2)
 
 
-@pytest.mark.parametrize("name,steps,lanes", [("parallel64", 400, 1), ("fan_curved_ragged", 60, 2),
-                                              ("fan_flat_ragged", 40, 4), ("cone_ragged", 30, 1),
-                                              ("cone_ragged", 30, 4), ("custom_sphere", 24, 2)])
-def test_brick_backprojection_parity(csgd, name, steps, lanes):
+@pytest.mark.parametrize("name,steps,lanes,shape", [
+    ("parallel64", 400, 1, -2), ("fan_curved_ragged", 60, 2, -3), ("fan_flat_ragged", 40, 4, -4),
+    ("cone_ragged", 30, 1, -2), ("cone_ragged", 30, 4, -3), ("cone_ragged", 30, 2, -4),
+    ("custom_sphere", 24, 2, -4)])
+def test_brick_backprojection_parity(csgd, name, steps, lanes, shape):
     """The brick backprojection (a CTA per brick of the tile walks the lines
     that cross it and sums in shared-memory fixed point; no ray table, the
     forward sets its own lines up) inside the solver: the same bounds against
@@ -270,7 +271,7 @@ def test_brick_backprojection_parity(csgd, name, steps, lanes):
     result on a second run (order-independent sums)."""
     from oracle import blocks as OB
     cfg = CASES[name]
-    x_gpu, x_ref, hist, o, rep, y = _solver_pair(csgd, cfg, steps, launch=(csgd.BRICK, lanes))
+    x_gpu, x_ref, hist, o, rep, y = _solver_pair(csgd, cfg, steps, launch=(shape, lanes))
     assert len(hist) == steps == len(o.log)
     mu_g = np.array([h["mu"] for h in hist])
     mu_o = np.array([l["mu"] for l in o.log])
@@ -280,7 +281,7 @@ def test_brick_backprojection_parity(csgd, name, steps, lanes):
     nnz_g = sum(h["nnz"] for h in hist)
     nnz_o = sum(OB.block_nnz(o.part, l["group"], l["j"]) for l in o.log)
     assert abs(nnz_g - nnz_o) <= 5e-3 * nnz_o, (nnz_g, nnz_o)
-    x2, *_ = _solver_pair(csgd, cfg, steps, launch=(csgd.BRICK, lanes))
+    x2, *_ = _solver_pair(csgd, cfg, steps, launch=(shape, lanes))
     np.testing.assert_array_equal(x_gpu, x2)
 
 
