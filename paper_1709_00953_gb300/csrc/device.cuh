@@ -294,18 +294,20 @@ __device__ __forceinline__ int walk(const float q[3], const float inv[3], const 
 
 // Whole traversal of the box: clip, then walk.
 // The 2D walk producing its crossings in batches of B: f(idx, len) receives
-// arrays of B entries once per batch; entries past the end of the walk have
-// length 0 and index b.base.  Same crossings, same arithmetic and the same
-// order as walk<2>; a batch lets the caller have B independent loads in flight.
-// No per-step bounds test: while the walk is alive its voxel is inside the box,
+// arrays of B entries once per batch.  Same crossings, same arithmetic and the
+// same order as walk<2>; a batch lets the caller have B independent loads in
+// flight.  No per-step bounds test: while t < tout the voxel is inside the box,
 // because a plane coordinate is an exact float (lo + integer) and the crossing
 // of the box's far face, (face - q) * inv, is bit-identical to the exit
-// parameter of clip, so the walk ends (t >= tout) before it could step past
+// parameter of clip, so the walk reaches t = tout before it could step past
 // it; a start index one voxel behind the line only gives a zero-length first
-// segment.  The caller still masks its loads with the box size, and the batch
+// segment.  Once t = tout every later entry of the batch has length exactly 0
+// (t stays at tout), so there is no per-step end test either: an entry of
+// length 0 carries a meaningless index, and the caller uses an index only
+// where the length is positive (and masks it with the box size).  The batch
 // count is capped at the number of faces the box has.
 template <int B, class F>
-__device__ __forceinline__ int walk2_batched(const float q[3], const float inv[3], const Box& b,
+__device__ __forceinline__ void walk2_batched(const float q[3], const float inv[3], const Box& b,
                                              float tin, float tout, F&& f) {
     int ix, iy;
     float px, py, tx, ty;
@@ -329,20 +331,15 @@ __device__ __forceinline__ int walk2_batched(const float q[3], const float inv[3
     const float fsx = (float)sx, fsy = (float)sy;
     const int max_batches = (b.n[0] + b.n[1] + 2) / B + 1;
     float tc = tin;
-    int cnt = 0;
-    bool alive = true;
-    for (int it = 0; alive && it < max_batches; ++it) {
+    for (int it = 0; tc < tout && it < max_batches; ++it) {
         int id[B];
         float ln[B];
 #pragma unroll
         for (int u = 0; u < B; ++u) {
             const bool bx = tx <= ty;
             const float t = fminf(bx ? tx : ty, tout);
-            const float len = fmaxf(t - tc, 0.f);
-            ln[u] = alive ? len : 0.f;
-            id[u] = alive ? idx : b.base;
-            cnt += ln[u] > 0.f;
-            alive = alive && t < tout;
+            ln[u] = fmaxf(t - tc, 0.f);
+            id[u] = idx;
             tc = t;
             idx += bx ? dsx : dsy;
             px += bx ? fsx : 0.f;
@@ -354,13 +351,12 @@ __device__ __forceinline__ int walk2_batched(const float q[3], const float inv[3
         }
         f(id, ln);
     }
-    return cnt;
 }
 
 // The 3D walk in batches of B, branch-free, with the same guarantees and the
 // same arithmetic as walk<3> (see walk2_batched).
 template <int B, class F>
-__device__ __forceinline__ int walk3_batched(const float q[3], const float inv[3], const Box& b,
+__device__ __forceinline__ void walk3_batched(const float q[3], const float inv[3], const Box& b,
                                              float tin, float tout, F&& f) {
     float p[3], tn[3], fs[3];
     int ds[3];
@@ -379,9 +375,7 @@ __device__ __forceinline__ int walk3_batched(const float q[3], const float inv[3
     }
     const int max_batches = (b.n[0] + b.n[1] + b.n[2] + 3) / B + 1;
     float tc = tin;
-    int cnt = 0;
-    bool alive = true;
-    for (int it = 0; alive && it < max_batches; ++it) {
+    for (int it = 0; tc < tout && it < max_batches; ++it) {
         int id[B];
         float ln[B];
 #pragma unroll
@@ -390,11 +384,8 @@ __device__ __forceinline__ int walk3_batched(const float q[3], const float inv[3
             const bool by = !bx && tn[1] <= tn[2];
             const bool bz = !bx && !by;
             const float t = fminf(bx ? tn[0] : (by ? tn[1] : tn[2]), tout);
-            const float len = fmaxf(t - tc, 0.f);
-            ln[u] = alive ? len : 0.f;
-            id[u] = alive ? idx : b.base;
-            cnt += ln[u] > 0.f;
-            alive = alive && t < tout;
+            ln[u] = fmaxf(t - tc, 0.f);
+            id[u] = idx;
             tc = t;
             idx += bx ? ds[0] : (by ? ds[1] : ds[2]);
             p[0] += bx ? fs[0] : 0.f;
@@ -409,7 +400,6 @@ __device__ __forceinline__ int walk3_batched(const float q[3], const float inv[3
         }
         f(id, ln);
     }
-    return cnt;
 }
 
 // Programmatic dependent launch.  pdl_trigger lets the next kernel of the

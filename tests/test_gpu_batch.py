@@ -97,15 +97,40 @@ def test_launch_shapes_change_rounding_only(mods):
         return x.cpu().numpy().astype(np.float64)
 
     ref = run(0, 0)
-    for c in list(range(1, 9)) + [csgd.SCATTER]:
+    for c in list(range(1, 9)) + [csgd.SCATTER] + list(csgd.BRICKS):
         for l in (1, 2, 4):
             x = run(c, l)
             assert np.sqrt(np.mean((x - ref) ** 2)) <= 1e-5 * max(np.abs(ref).max(), 1e-12), (c, l)
     c, l = s.autotune(8)
-    assert (c == csgd.SCATTER or 1 <= c <= 8) and l in (1, 2, 4)
+    assert (c == csgd.SCATTER or c in csgd.BRICKS or 1 <= c <= 8) and l in (1, 2, 4)
     with pytest.raises(RuntimeError):
         s.set_launch(9, 0)
     with pytest.raises(RuntimeError):
-        s.set_launch(-2, 0)
+        s.set_launch(min(csgd.BRICKS) - 1, 0)
     with pytest.raises(RuntimeError):
         s.set_launch(0, 3)
+
+
+def test_batch_matches_oracle(mods):
+    """Batched solves against the FP64 oracle: three uneven problems of the
+    batched workload's kind (curved fans, 8 view blocks x 4 x 4 tiles,
+    density-weighted choice), autotuned and solved together in one graph
+    launch, each within RMSE 1e-4 of the oracle's literal run of its own
+    schedule and step count."""
+    from oracle.blocks import Partition as OPart
+    from oracle.geometry import Geometry as OGeom
+    from oracle.solver import OracleSolver
+    csgd, batch = mods
+    probs = _problems(batch, 3)
+    b = batch.Batch(probs, autotune=True)
+    b.launch()
+    torch.cuda.synchronize()
+    for p in probs:
+        cfg = p.cfg
+        og = OGeom(**cfg["geom"])
+        op = OPart(og, cfg["part"]["tiles"], cfg["part"]["view_blocks"], cfg["part"]["det_blocks"])
+        o = OracleSolver(op, cfg["solver"], p.y.cpu().numpy().astype(np.float64))
+        xo = o.run(p.steps)
+        xg = p.x.cpu().numpy().astype(np.float64)
+        assert np.abs(xo).max() > 0
+        assert float(np.sqrt(np.mean((xg - xo) ** 2))) <= 1e-4, cfg["name"]
