@@ -423,6 +423,14 @@ void plan_step(csgd_solver* S, Plan* pl, int j, const std::vector<int>& group, i
     int64_t rays = build_work_items(p, group.data(), (int)group.size(), j, slot, &pl->items);
     sd.w1 = (int32_t)pl->items.size();
     sd.n_rays = rays;
+    double terms = 0.0;
+    for (int32_t w = sd.w0; w < sd.w1; ++w) {
+        const DevVT& e = p.vt(pl->items[w].view, j);
+        const double tu = std::floor(std::min(2.0 * e.hw_u, 4096.0)) + 2.0;
+        const double tv = p.g->dim == 3 ? std::floor(std::min(2.0 * e.hw_v, 4096.0)) + 2.0 : 1.0;
+        terms += tu * tv;
+    }
+    sd.terms = (float)terms;
     sd.step = S->steps_done;
     sd.beta = beta_of(S, j, group);
     pl->steps.push_back(sd);
@@ -714,7 +722,7 @@ int32_t csgd_backproject_block_noalloc(const csgd_partition* Pc, const int32_t* 
         it.step.n_rays = rays;
         it.step.step = 0;
         it.step.beta = 0.0;
-        it.step.pad = 0;
+        it.step.terms = 0.f;
         it.n = cnt;
         cudaError_t e = launch_backproject_inline(p.dg, p.tiles_h[j], it, r, g,
                                                   first ? accumulate : 1, table, P->sm_count, s);

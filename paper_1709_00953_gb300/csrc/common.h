@@ -93,7 +93,8 @@ struct alignas(16) RayRec {
 struct StepDesc {
     int32_t j;             // tile
     int32_t w0, w1;        // work items [w0, w1)
-    int32_t pad;
+    float terms;           // bound on the lines of the step through one voxel of the
+                           // tile (per view, the bins within hw_u, hw_v of the voxel)
     int64_t n_rays;        // rays covered by the work items
     int64_t step;          // global step index (for the history)
     double beta;

@@ -146,14 +146,12 @@ __device__ __forceinline__ bool clip_sliver(const float q[3], const float inv[3]
     return t0 < t1;
 }
 
-// Chord (voxel units) of the exact line of bin (ku, kv) of view `view` through
-// tile t, from the FP64 frame (the line the per (view, tile) FP32 constants
-// round); at most 0 when the line misses the tile.  Half-open faces as in the
-// walk: a line parallel to an axis meets the tile when lo <= q < hi.
-__device__ __forceinline__ double exact_chord(const DevGeom& G, int view, int ku, int kv,
-                                           const DevTile& t) {
+// The exact line of bin (ku, kv) of view `view`, in FP64 from the unrounded
+// frame (the line the per (view, tile) FP32 constants round), in the
+// coordinates of tile t (voxel units, centred on the tile): p0 + s d.
+__device__ __forceinline__ void exact_line(const DevGeom& G, int view, int ku, int kv,
+                                           const DevTile& t, double p0[3], double d[3]) {
     const DevView64& V = G.views64[view];
-    double p0[3], d[3];
     if (G.kind == PARALLEL_2D) {
         const double s = ((double)ku - (double)G.cu) * G.pu_d;
 #pragma unroll
@@ -178,6 +176,15 @@ __device__ __forceinline__ double exact_chord(const DevGeom& G, int view, int ku
             d[a] = V.sdd * V.dc[a] + u * V.eu[a] + w * V.ev[a];
         }
     }
+}
+
+// Chord (voxel units) of that exact line through tile t; at most 0 when it
+// misses the tile.  Half-open faces as in the walk: a line parallel to an
+// axis meets the tile when lo <= q < hi.
+__device__ __forceinline__ double exact_chord(const DevGeom& G, int view, int ku, int kv,
+                                              const DevTile& t) {
+    double p0[3], d[3];
+    exact_line(G, view, ku, kv, t, p0, d);
     double t0 = -INFINITY, t1 = INFINITY, dn = 0.0;
     for (int a = 0; a < G.dim; ++a) {
         const double lo = -0.5 * (double)t.n[a], hi = 0.5 * (double)t.n[a];
@@ -191,6 +198,24 @@ __device__ __forceinline__ double exact_chord(const DevGeom& G, int view, int ku
         }
     }
     return (t1 - t0) * sqrt(dn);
+}
+
+// Coordinate along axis ax of a line parallel to that axis's planes, placed on
+// the same side of its nearest voxel face as the exact (FP64) line: the FP32
+// set-up may put a line that lies exactly on a face (a view at a multiple of
+// 90 degrees and a bin on a face), or within rounding of one, on either side,
+// and so in the wrong voxel column (or tile) over its whole length.  A line
+// exactly on a face goes to the voxel above it (half-open voxels), one ulp
+// above the face, so that (face - q) / d is never 0 / 0 either.
+__device__ __forceinline__ float parallel_coord(const DevGeom& G, int view, int ku, int kv,
+                                                const DevTile& t, int ax) {
+    double p0[3], d[3];
+    exact_line(G, view, ku, kv, t, p0, d);
+    const double e = p0[ax];
+    const double hn = 0.5 * (double)t.n[ax];
+    const double f = rint(e + hn) - hn;  // nearest face (an exact float)
+    const float ff = (float)f, qa = (float)e;
+    return e >= f ? fmaxf(qa, nextafterf(ff, INFINITY)) : fminf(qa, nextafterf(ff, -INFINITY));
 }
 
 // Incremental Siddon walk of the line q + t d through the box over t in

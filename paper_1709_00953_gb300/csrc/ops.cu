@@ -12,7 +12,7 @@
 //                     No atomics.
 //   k_backproject_scatter + k_scatter_convert
 //                     the same g_J ray-driven: every ray walks the tile and adds
-//                     len * r to 64-bit fixed-point sums with integer atomics
+//                     len * r to 32-bit fixed-point sums with integer atomics
 //                     (exact, order-independent), then one pass converts them.
 //   k_forward_dual    p = A x_J and q = A g_J in one walk per ray, ||q||^2 per
 //                     CTA, the step length mu computed by the last CTA of each
@@ -62,17 +62,12 @@ __device__ __forceinline__ void table_ray(const DevGeom& G, int view, const DevV
     float d[3];
     ray_setup(G, V, E, ku, kv, q, d);
     reciprocal(d, inv);
-    // A ray parallel to axis ax whose q_ax lies exactly on a voxel face moves
-    // one ulp up: it meets the same voxels (a face belongs to the voxel above
-    // it, for the walk as for the oracle) and (face - q_ax) / d_ax is never 0 / 0.
+    // a line parallel to the planes of axis ax (d exactly 0 there, in FP32 as
+    // in FP64: a view at a multiple of 90 degrees) is put on the exact line's
+    // side of its nearest voxel face, one ulp above a face it lies on
 #pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) {
-        if (isinf(inv[ax])) {
-            const float hn = 0.5f * (float)tile.n[ax];
-            const float face = (float)__float2int_rn(q[ax] + hn) - hn;
-            if (q[ax] == face) q[ax] = nextafterf(q[ax], INFINITY);
-        }
-    }
+    for (int ax = 0; ax < DIM; ++ax)
+        if (isinf(inv[ax])) q[ax] = parallel_coord(G, view, ku, kv, tile, ax);
     // a line that only touches the tile (see exact_chord) gets no support in it
     const Box b = tile_box(tile, DIM, 0, tile.n[0], tile.n[0] * tile.n[1]);
     float tin, tout;
@@ -126,15 +121,12 @@ __device__ __forceinline__ void forward_single(const DevGeom& G, const WorkItem*
         int kv = it.v0 + (int)(within / wu);
         const DevView V = G.views[it.view];
         const DevVT E = G.vt[(int64_t)it.view * G.n_tiles + sd.j];
-        float q[3], d[3], inv[3];
-        ray_setup(G, V, E, ku, kv, q, d);
-        reciprocal(d, inv);
+        float q[3], inv[3];
+        table_ray<DIM>(G, it.view, V, E, t, ku, kv, q, inv);  // the solver's line set-up
         int base = (t.lo[2] * G.ny + t.lo[1]) * G.nx + t.lo[0];
         Box b = tile_box(t, DIM, base, G.nx, G.nx * G.ny);
         float tin, tout;
-        bool sliver;
-        if (clip_sliver<DIM>(q, inv, b, &tin, &tout, &sliver) &&
-            !(sliver && exact_chord(G, it.view, ku, kv, t) <= kTouchChord)) {
+        if (clip<DIM>(q, inv, b, &tin, &tout)) {
             float dt = (tout - tin) * (1.0f / L);
             float t0 = sub == 0 ? tin : fmaf((float)sub, dt, tin);
             float t1 = sub == L - 1 ? tout : fmaf((float)(sub + 1), dt, tin);
@@ -842,7 +834,7 @@ __global__ void __maxnreg__(64) k_backproject_solver(
 // ---------------------------------------------------------------------------
 // Ray-driven backprojection (scatter).  Every ray of a slot walks the tile as
 // in the dual forward (same crossings, so the same lengths) and adds len * r_i
-// to a 64-bit fixed-point accumulator of its voxel with an integer atomic: the
+// to a 32-bit fixed-point accumulator of its voxel with an integer atomic: the
 // sum of the slot's FP32 products len * r_i is then exact (below the fixed
 // point's resolution) and independent of the order of the additions, so the
 // result is deterministic.  A conversion pass turns the accumulator into the
@@ -854,17 +846,20 @@ struct ScatterArgs {
     DevGeom G;
     const StepDesc* steps;
     int first;
+    float lane_factor;  // 2 when the lanes of a line may split its segment in a voxel
     SolverBuffers sb;
 };
 
 // Fixed-point exponent S of a slot (term = round(2^S * len * r)): a line
-// crosses a unit voxel over at most sqrt(3) < 2, so every term is below
-// 2 max|r| 2^S < 2^30 with S = 30 - e, 2 max|r| < 2^e, and fits a 32-bit
-// conversion (FP32 pipe; the 64-bit one runs on the slow FP64 pipe).  A voxel
-// sums at most one term per ray of the slot, below 2^30 n_rays < 2^63.  The
-// resolution, 2^-30 of the largest possible term, is far below FP32 rounding.
-__device__ __forceinline__ int scatter_shift(unsigned rmax_bits) {
-    const float bound = __uint_as_float(rmax_bits) * 2.0f;
+// crosses a unit voxel over at most sqrt(3) < 2, so a term is below
+// 2 max|r| 2^S, and a voxel receives at most `terms` of them (twice that when
+// the lanes of a line can split its segment in a voxel), so with
+// terms 2 max|r| < 2^e and S = 30 - e every sum stays below 2^30 and fits the
+// 32-bit accumulator.  The resolution, 2^-S, is about 2 terms max|r| 2^-30:
+// far below FP32 rounding of the sum for the tens to hundreds of terms a
+// step's views put into one voxel.
+__device__ __forceinline__ int scatter_shift(unsigned rmax_bits, float terms) {
+    const float bound = __uint_as_float(rmax_bits) * 2.0f * fmaxf(1.0f, terms);
     int e = 0;
     frexpf(bound, &e);  // bound < 2^e (e = 0 for bound = 0)
     return min(100, max(-100, 30 - e));
@@ -882,8 +877,8 @@ __global__ void __maxnreg__(64) k_backproject_scatter(const ScatterArgs a) {
     const DevTile t = G.tiles[sd.j];
     const int nvox = t.n[0] * t.n[1] * t.n[2];
     pdl_wait();  // the ray table and the slot's max |r| come from the previous kernel
-    unsigned long long* __restrict__ acc = a.sb.acc + (int64_t)slot * a.sb.g_stride;
-    const float sc = pow2f(scatter_shift(a.sb.rmax[slot]));
+    int* __restrict__ acc = reinterpret_cast<int*>(a.sb.acc) + (int64_t)slot * a.sb.g_stride;
+    const float sc = pow2f(scatter_shift(a.sb.rmax[slot], sd.terms * a.lane_factor));
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t k = gid / L;
     const int sub = (int)(gid % L);
@@ -909,9 +904,8 @@ __global__ void __maxnreg__(64) k_backproject_scatter(const ScatterArgs a) {
                         ++nz;
                         first_id = first_id < 0 ? id[u] : first_id;
                         last_id = id[u];
-                        if (rs != 0.f && (unsigned)id[u] < (unsigned)nvox)
-                            atomicAdd(acc + id[u],
-                                      (unsigned long long)(long long)__float2int_rn(ln[u] * rs));
+                        const int term = __float2int_rn(ln[u] * rs);
+                        if (term && (unsigned)id[u] < (unsigned)nvox) atomicAdd(acc + id[u], term);
                     }
                 }
             };
@@ -952,21 +946,16 @@ __global__ void __launch_bounds__(kConvThreads) k_scatter_convert(const ScatterA
     const DevTile t = G.tiles[sd.j];
     const int nvox = t.n[0] * t.n[1] * t.n[2];
     pdl_wait();
-    const float isc = pow2f(-scatter_shift(a.sb.rmax[slot]));
-    unsigned long long* acc = a.sb.acc + (int64_t)slot * a.sb.g_stride;
+    // the same exponent as the scatter's (same bound, same lane factor)
+    const float isc = pow2f(-scatter_shift(a.sb.rmax[slot], sd.terms * a.lane_factor));
+    int* acc = reinterpret_cast<int*>(a.sb.acc) + (int64_t)slot * a.sb.g_stride;
     float2* gout = reinterpret_cast<float2*>(a.sb.g) + (int64_t)slot * a.sb.g_stride;
     const float* xt = a.sb.x + t.voff;
     float gg = 0.f;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += gridDim.x * blockDim.x) {
-        const long long s = (long long)acc[v];
-        acc[v] = 0ull;
-        // 64-bit integer to float on the FP32 pipe: the magnitude's high word
-        // times 2^32 plus its low word, rounded in the fused multiply-add
-        // (exact rounding below 2^32, within one ulp above), then the sign
-        const unsigned long long m = s < 0 ? 0ull - (unsigned long long)s : (unsigned long long)s;
-        const float mf = fmaf((float)(unsigned)(m >> 32), 4294967296.0f,
-                              (float)(unsigned)(m & 0xffffffffull));
-        const float g = (s < 0 ? -mf : mf) * isc * G.h;
+        const int s = acc[v];
+        acc[v] = 0;
+        const float g = (float)s * isc * G.h;
         gout[v] = make_float2(xt[v], g);
         gg = fmaf(g, g, gg);
     }
@@ -1685,6 +1674,7 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
         sa.G = G;
         sa.steps = steps;
         sa.first = b.first;
+        sa.lane_factor = L > 1 ? 2.f : 1.f;
         sa.sb = sb;
         dim3 grid((unsigned)nb, b.nslots);
         if (G.dim == 2) {

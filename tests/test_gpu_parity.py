@@ -93,6 +93,12 @@ CASES = {
     "fan_flat_ragged": C.small_fan2d(n=80, views=40, nu=120, tiles=(2, 3), vb=4, du=3,
                                      curved=False),
     "cone_ragged": C.small_cone3d(n=24, views=12, nd=40, tiles=(2, 2, 3), du=2, dv=2),
+    # 159 curved bins (the centre bin's line through the image centre), 106^2 in
+    # 4 x 4 tiles (the centre is a corner of four tiles) and 108 views (one at
+    # 90 degrees): that view's centre line lies exactly on a tile face, which
+    # FP32 rounding alone would put on either side of it
+    "fan_curved_centre_face": C.batch_fan2d(n_problems=3, n_range=(64, 160), views_range=(30, 120),
+                                            epochs=2, seed=42)[2],
     "custom_sphere": dict(
         C.small_cone3d(n=20, views=10, nd=36, tiles=(2, 3, 2), du=1, dv=2),
         geom=dict(kind="custom3d", n=(20, 20, 20), h=1.0, nu=36, nv=36, pu=1.8, pv=1.8,
@@ -102,7 +108,10 @@ CASES = {
 
 def _groups(op):
     m, n = op.n_row_blocks, op.n_col_blocks
-    return [([0], 0), ([m - 1], n - 1), (list(range(0, m, 2)), n // 2), ([m // 2], 1 % n)]
+    out = [([0], 0), ([m - 1], n - 1), (list(range(0, m, 2)), n // 2), ([m // 2], 1 % n)]
+    if n == 16 and m == 8:  # 4 x 4 tiles: a centre tile (a corner at the image centre)
+        out.append(([2], 13))
+    return out
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -211,7 +220,7 @@ def _solver_pair(csgd, cfg, steps, launch=None):
 
 @pytest.mark.parametrize("name,steps", [("parallel64", 400), ("fan_curved_ragged", 60),
                                         ("fan_flat_ragged", 40), ("cone_ragged", 30),
-                                        ("custom_sphere", 24)])
+                                        ("custom_sphere", 24), ("fan_curved_centre_face", 128)])
 def test_solver_parity(csgd, name, steps):
     cfg = CASES[name]
     x_gpu, x_ref, hist, o, rep, y = _solver_pair(csgd, cfg, steps)
