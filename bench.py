@@ -331,6 +331,8 @@ def run_gpu(args, cfg, world, rank, local):
     yt = torch.tensor(y, device=dev)
     stream = torch.cuda.current_stream()
     solver = csgd.Solver(p, cfg["solver"], yt)
+    if args.launch:
+        solver.set_launch(*(int(v) for v in args.launch.split(",")))
     steps = cfg["steps"]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 

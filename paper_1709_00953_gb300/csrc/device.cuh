@@ -361,18 +361,20 @@ __device__ __forceinline__ void walk2_batched(const float q[3], const float inv[
         float ln[B];
 #pragma unroll
         for (int u = 0; u < B; ++u) {
-            const bool bx = tx <= ty;
-            const float t = fminf(bx ? tx : ty, tout);
+            const float t = fminf(fminf(tx, ty), tout);
             ln[u] = fmaxf(t - tc, 0.f);
             id[u] = idx;
             tc = t;
-            idx += bx ? dsx : dsy;
-            px += bx ? fsx : 0.f;
-            py += bx ? 0.f : fsy;
-            const float nxt = (px - q[0]) * inv[0];
-            const float nyt = (py - q[1]) * inv[1];
-            tx = bx ? nxt : tx;
-            ty = bx ? ty : nyt;
+            // only the axis whose plane is crossed advances (x on ties)
+            if (tx <= ty) {
+                idx += dsx;
+                px += fsx;
+                tx = (px - q[0]) * inv[0];
+            } else {
+                idx += dsy;
+                py += fsy;
+                ty = (py - q[1]) * inv[1];
+            }
         }
         f(id, ln);
     }
@@ -405,23 +407,25 @@ __device__ __forceinline__ void walk3_batched(const float q[3], const float inv[
         float ln[B];
 #pragma unroll
         for (int u = 0; u < B; ++u) {
-            const bool bx = tn[0] <= tn[1] && tn[0] <= tn[2];
-            const bool by = !bx && tn[1] <= tn[2];
-            const bool bz = !bx && !by;
-            const float t = fminf(bx ? tn[0] : (by ? tn[1] : tn[2]), tout);
+            const float m = fminf(fminf(tn[0], tn[1]), tn[2]);
+            const float t = fminf(m, tout);
             ln[u] = fmaxf(t - tc, 0.f);
             id[u] = idx;
             tc = t;
-            idx += bx ? ds[0] : (by ? ds[1] : ds[2]);
-            p[0] += bx ? fs[0] : 0.f;
-            p[1] += by ? fs[1] : 0.f;
-            p[2] += bz ? fs[2] : 0.f;
-            const float nx = (p[0] - q[0]) * inv[0];
-            const float ny = (p[1] - q[1]) * inv[1];
-            const float nz = (p[2] - q[2]) * inv[2];
-            tn[0] = bx ? nx : tn[0];
-            tn[1] = by ? ny : tn[1];
-            tn[2] = bz ? nz : tn[2];
+            // only the axis whose plane is crossed advances (x, then y, on ties)
+            if (tn[0] == m) {
+                idx += ds[0];
+                p[0] += fs[0];
+                tn[0] = (p[0] - q[0]) * inv[0];
+            } else if (tn[1] == m) {
+                idx += ds[1];
+                p[1] += fs[1];
+                tn[1] = (p[1] - q[1]) * inv[1];
+            } else {
+                idx += ds[2];
+                p[2] += fs[2];
+                tn[2] = (p[2] - q[2]) * inv[2];
+            }
         }
         f(id, ln);
     }
