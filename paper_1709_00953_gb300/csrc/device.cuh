@@ -65,10 +65,11 @@ struct Box {
     int base;
 };
 
-// Reciprocal direction used by every plane crossing: 1/d, infinite where d = 0.
+// Reciprocal direction used by every plane crossing: 1/d, infinite where d = 0
+// (__frcp_rn: the correctly rounded reciprocal, the value 1.0f / d has).
 __device__ __forceinline__ void reciprocal(const float d[3], float inv[3]) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) inv[a] = d[a] != 0.f ? 1.0f / d[a] : INFINITY;
+    for (int a = 0; a < 3; ++a) inv[a] = d[a] != 0.f ? __frcp_rn(d[a]) : INFINITY;
 }
 
 // Parameter interval [tin, tout) of the line q + t d inside the box, given

@@ -318,7 +318,7 @@ struct TableArgs {
     const float* r;
     RayRec* table;       // [slot][ray slot]
     int64_t slot_stride;
-    unsigned* rmax;      // [slot] max |r| bits (scatter backprojection), or null
+    unsigned* rmax;      // [slot] max |r| bits (k_slot_rmax)
 };
 
 // The first kTablePre rays of a thread are set up before waiting for the
@@ -345,14 +345,12 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
             table_ray<DIM>(G, it.view, V, E, tile, it.u0 + k % wu, it.v0 + k / wu, pq[p], pi[p]);
     }
     pdl_wait();  // r and the table buffer belong to earlier kernels until here
-    float rm = 0.f;  // max |r| of this thread's rays
 #pragma unroll
     for (int p = 0; p < kTablePre; ++p) {
         const int k = k0 + p * stride;
         if (k < nr) {
             const int64_t ray = ray_index(G, it.view, it.u0 + k % wu, it.v0 + k / wu);
             const float rv = __ldg(a.r + ray);
-            rm = fmaxf(rm, fabsf(rv));
             *reinterpret_cast<float4*>(dst[k].a) = make_float4(pq[p][0], pq[p][1], pi[p][0], pi[p][1]);
             *reinterpret_cast<float4*>(dst[k].b) =
                 make_float4(rv, pq[p][2], pi[p][2], __int_as_float((int)ray));
@@ -365,15 +363,9 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
         table_ray<DIM>(G, it.view, V, E, tile, ku, kv, q, inv);
         const int64_t ray = ray_index(G, it.view, ku, kv);
         const float rv = __ldg(a.r + ray);
-        rm = fmaxf(rm, fabsf(rv));
         *reinterpret_cast<float4*>(dst[k].a) = make_float4(q[0], q[1], inv[0], inv[1]);
         *reinterpret_cast<float4*>(dst[k].b) =
             make_float4(rv, q[2], inv[2], __int_as_float((int)ray));
-    }
-    if (a.rmax) {
-        // non-negative floats order like their bit patterns
-        const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(rm));
-        if ((threadIdx.x & 31) == 0 && wm) atomicMax(a.rmax + it.slot, wm);
     }
 }
 
@@ -389,6 +381,24 @@ __global__ void __launch_bounds__(256) k_ray_table_solver(const TableArgs a,
     pdl_trigger();
     const WorkItem it = items[a.w_begin + blockIdx.x];
     ray_table_item<DIM>(a, it);
+}
+
+// max |r| per slot over the rays of the batch's work items (the scatter's
+// fixed-point scale when it sets its lines up itself): one CTA row per item.
+__global__ void __launch_bounds__(256) k_slot_rmax(const TableArgs a,
+                                                   const WorkItem* __restrict__ items) {
+    pdl_trigger();
+    const WorkItem it = items[a.w_begin + blockIdx.x];
+    const DevGeom& G = a.G;
+    const int wu = it.u1 - it.u0;
+    const int nr = wu * (it.v1 - it.v0);
+    pdl_wait();  // r belongs to earlier kernels until here
+    float rm = 0.f;
+    for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < nr; k += gridDim.y * blockDim.x)
+        rm = fmaxf(rm, fabsf(a.r[ray_index(G, it.view, it.u0 + k % wu, it.v0 + k / wu)]));
+    // non-negative floats order like their bit patterns
+    const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(rm));
+    if ((threadIdx.x & 31) == 0 && wm) atomicMax(a.rmax + it.slot, wm);
 }
 
 struct BPArgs {
@@ -844,6 +854,7 @@ __global__ void __maxnreg__(64) k_backproject_solver(
 // ---------------------------------------------------------------------------
 struct ScatterArgs {
     DevGeom G;
+    const WorkItem* items;
     const StepDesc* steps;
     int first;
     float lane_factor;  // 2 when the lanes of a line may split its segment in a voxel
@@ -876,21 +887,31 @@ __global__ void __maxnreg__(64) k_backproject_scatter(const ScatterArgs a) {
     const StepDesc sd = a.steps[a.first + slot];
     const DevTile t = G.tiles[sd.j];
     const int nvox = t.n[0] * t.n[1] * t.n[2];
-    pdl_wait();  // the ray table and the slot's max |r| come from the previous kernel
-    int* __restrict__ acc = reinterpret_cast<int*>(a.sb.acc) + (int64_t)slot * a.sb.g_stride;
-    const float sc = pow2f(scatter_shift(a.sb.rmax[slot], sd.terms * a.lane_factor));
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t k = gid / L;
     const int sub = (int)(gid % L);
+    const bool active = k < sd.n_rays;
+    float q[3], inv[3];
+    int ray = 0;
+    // the line set up here, before the wait (geometry only), as the dual
+    // forward sets it up
+    if (active) {
+        const int w = find_item(a.items, sd.w0, sd.w1, k);
+        const WorkItem it = a.items[w];
+        const int within = (int)(k - it.ray_off);
+        const int wu = it.u1 - it.u0;
+        const int ku = it.u0 + within % wu, kv = it.v0 + within / wu;
+        table_ray<DIM>(G, it.view, G.views[it.view], G.vt[(int64_t)it.view * G.n_tiles + sd.j],
+                       t, ku, kv, q, inv);
+        ray = (int)ray_index(G, it.view, ku, kv);
+    }
+    pdl_wait();  // r and the slot's max |r| come from earlier kernels
+    int* __restrict__ acc = reinterpret_cast<int*>(a.sb.acc) + (int64_t)slot * a.sb.g_stride;
+    const float sc = pow2f(scatter_shift(a.sb.rmax[slot], sd.terms * a.lane_factor));
     int nz = 0;
     int first_id = -1, last_id = -1;  // voxels of the lane's first and last non-zero
-    if (k < sd.n_rays) {
-        const RayRec* rp = a.sb.table + (int64_t)slot * a.sb.table_stride + k;
-        const float4 ra = *reinterpret_cast<const float4*>(rp->a);
-        const float4 rb = *reinterpret_cast<const float4*>(rp->b);
-        const float q[3] = {ra.x, ra.y, rb.y};
-        const float inv[3] = {ra.z, ra.w, rb.z};
-        const float rs = rb.x * sc;  // (len * r) * 2^S rounds as len * (r * 2^S)
+    if (active) {
+        const float rs = __ldcg(a.sb.r + ray) * sc;  // (len * r) * 2^S rounds as len * (r * 2^S)
         Box b = tile_box(t, DIM, 0, t.n[0], t.n[0] * t.n[1]);
         float tin, tout;
         if (clip<DIM>(q, inv, b, &tin, &tout)) {
@@ -1644,9 +1665,17 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     ta.r = sb.r;
     ta.table = sb.table;
     ta.slot_stride = sb.table_stride;
-    ta.rmax = scatter ? sb.rmax : nullptr;
-    cudaError_t e = brick ? cudaSuccess
-                          : launch_table(G, b.n_items, b.max_item_rays, s, ta, nullptr, items);
+    ta.rmax = sb.rmax;
+    // the gather reads a ray table; the scatter and the bricks set their lines
+    // up themselves (the scatter after a pass for each slot's max |r|)
+    cudaError_t e = cudaSuccess;
+    if (scatter) {
+        if (b.n_items > 0)
+            e = launch_pdl(k_slot_rmax, dim3((unsigned)b.n_items, (unsigned)item_rows(b.max_item_rays)),
+                           dim3(256), s, ta, items);
+    } else if (!brick) {
+        e = launch_table(G, b.n_items, b.max_item_rays, s, ta, nullptr, items);
+    }
     if (e != cudaSuccess) return e;
     int n_gg = plan.blocks;
     if (brick) {
@@ -1672,6 +1701,7 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     } else if (scatter) {
         ScatterArgs sa;
         sa.G = G;
+        sa.items = items;
         sa.steps = steps;
         sa.first = b.first;
         sa.lane_factor = L > 1 ? 2.f : 1.f;
@@ -1721,8 +1751,8 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     f.n_gg = n_gg;
     f.sb = sb;
     dim3 grid((unsigned)nb, b.nslots);
-    // the brick backprojection builds no ray table: the forward sets its lines up
-    if (brick) e = launch_forward<false>(G.dim, L, grid, s, f);
+    // only the gather builds a ray table; otherwise the forward sets its lines up
+    if (brick || scatter) e = launch_forward<false>(G.dim, L, grid, s, f);
     else e = launch_forward<true>(G.dim, L, grid, s, f);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
