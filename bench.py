@@ -554,9 +554,17 @@ def run_batch(args, world, rank, local):
     t_tune = time.perf_counter() - t_tune
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def executor():
+        b.launch(stream)
+
+    forms = {"persistent": executor, "graph_of_graphs": lambda: b.launch_graphs(stream),
+             "sequential_graphs": lambda: b.launch_sequential_graphs(stream),
+             "one_by_one": lambda: b.solve_one_by_one(stream)}
     for _ in range(args.warmup):
-        b.launch()
-        b.solve_one_by_one()
+        for fn in forms.values():
+            fn()
+        b.status()
     torch.cuda.synchronize()
     # updates per round (kernel-counted non-zeros of every problem's solve)
     nnz = 0
@@ -564,50 +572,58 @@ def run_batch(args, world, rank, local):
         p.solver.reset(p.y)
         rep = p.solver.solve(p.steps, p.x, report=True)
         nnz += rep["nnz"]
-    # batched: one graph launch solves all problems
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(c) for a, c in ev)
+
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        b.launch(stream)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    ms = {"persistent": timed(executor)}
     ck = clocks.stop()
-    ms_b = sum(a.elapsed_time(c) for a, c in ev)
-    xb = [p.x.clone() for p in probs]
-    # one by one: each problem's plain solve, synchronised before the next
-    t0 = time.perf_counter()
-    ev1 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    ms_1 = 0.0
-    for k in range(args.steps):
-        flush.zero_()
-        ev1[0].record(stream)
-        b.solve_one_by_one(stream)
-        ev1[1].record(stream)
-        torch.cuda.synchronize()
-        ms_1 += ev1[0].elapsed_time(ev1[1])
-    same = all(torch.equal(p.x, x) for p, x in zip(probs, xb))
+    b.status()
+    x_exec = [p.x.clone() for p in probs]
+    for name in ("graph_of_graphs", "sequential_graphs", "one_by_one"):
+        ms[name] = timed(forms[name])
+    x_plain = [p.x.clone() for p in probs]
+    b.launch_graphs(stream)
+    torch.cuda.synchronize()
+    graphs_equal = all(torch.equal(p.x, x) for p, x in zip(probs, x_plain))
+    # the executor's solutions against the one-by-one ones (the same RMSE to rounding)
+    rel = max(float(torch.sqrt(torch.mean((xe.double() - xp.double()) ** 2)))
+              / max(float(xp.abs().max()), 1e-30) for xe, xp in zip(x_exec, x_plain))
     n = len(probs)
+    rate = {k: 1e3 * n * args.steps / v for k, v in ms.items()}
+    info = b.executor.info()
     line = {
-        "metric": "solves/s at fixed step count (64 uneven fan problems, one graph launch)",
-        "value": 1e3 * n * args.steps / ms_b, "unit": "solves/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b / args.steps,
+        "metric": "solves/s at fixed step count (64 uneven fan problems, one persistent launch)",
+        "value": rate["persistent"], "unit": "solves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms["persistent"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "batch_fan64", "problems": n,
                    "sizes": "n ~ U[128,1024], views ~ U[60,900], 3 epochs each",
                    "l2": "flushed (256 MB write) before each step"},
-        "one_by_one": {"value": 1e3 * n * args.steps / ms_1, "unit": "solves/s",
-                       "ms_per_step": ms_1 / args.steps},
-        "speedup_vs_one_by_one": ms_1 / ms_b,
-        "updates_per_s": 3.0 * nnz * args.steps / (ms_b / 1e3),
-        "identical_results": same,
+        "forms": {k: {"solves_per_s": rate[k], "ms_per_step": ms[k] / args.steps} for k in ms},
+        "speedup_vs_one_by_one": ms["one_by_one"] / ms["persistent"],
+        "speedup_vs_sequential_graphs": ms["sequential_graphs"] / ms["persistent"],
+        "updates_per_s": 3.0 * nnz * args.steps / (ms["persistent"] / 1e3),
+        "executor": dict(info, note="tasks = the kernels of all solves; units = their thread "
+                                    "blocks; blocks = resident executor blocks"),
+        "equal_rmse": {"graph_forms_bit_identical_to_one_by_one": graphs_equal,
+                       "persistent_max_relative_rmse_vs_one_by_one": rel},
         "launch_shapes": {"autotuned": True, "seconds": t_tune,
                           "view_groups": sorted(collections.Counter(p.shapes[0] for p in probs).items()),
-                          "lanes_per_ray": sorted(collections.Counter(p.shapes[1] for p in probs).items())},
+                          "lanes_per_ray": sorted(collections.Counter(p.shapes[1] for p in probs).items()),
+                          "persistent": "one lane per ray, 256-thread blocks, 4 view groups"},
     }
     if ck:
         line["clocks"] = ck

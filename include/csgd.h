@@ -321,11 +321,53 @@ int32_t csgd_graph_batch_create(csgd_graph* const* parts, int32_t n, csgd_graph*
 int32_t csgd_graph_launch(csgd_graph* graph, csgd_stream stream);
 int32_t csgd_graph_destroy(csgd_graph* graph);
 
+/* Many solves in ONE persistent kernel launch with a device work queue (the
+ * paper's parallel block steps, Sec. II-F, taken across problems: the paper
+ * has no batching of its own).  For every solver the whole solve is planned as
+ * in csgd_solver_graph_create (reset, n_steps[k] steps of the schedule from
+ * the seed, the epoch closed at the end, x to the device array x_out[k] if not
+ * NULL); each kernel of it becomes a task of thread blocks, and the problems'
+ * task lists are interleaved.  One launch of the executor (captured with the
+ * solvers' resets in a CUDA graph) runs all of them: each block takes the next
+ * block of work from a ticket counter, waits until its problem's earlier
+ * kernels have completed, runs it and counts it as done.  Every such wait is
+ * bounded by wait_limit_ns of GPU time (0 selects 2 s); a wait that runs out
+ * stops the launch and csgd_batch_status returns CSGD_ERR_TIMEOUT.
+ * The executor runs every solve with one lane per ray, 256-thread blocks and,
+ * for the gather backprojection, 4 view groups per block (bricks run as the
+ * scatter): results equal the solvers' own solves to rounding.  The solvers
+ * must stay alive, on one device, all 2D or all 3D, and must not be used
+ * otherwise while the batch may run (the batch keeps their planned schedules
+ * on the device).
+ *   stall_last_task: a test hook: the last task of the first problem waits for
+ *   a block of work that never completes, so that the bound on the wait can be
+ *   checked; 0 in normal use. */
+typedef struct csgd_batch csgd_batch;
+typedef struct {
+    int64_t wait_limit_ns;
+    int32_t stall_last_task;
+    int32_t reserved;
+} csgd_batch_params;
+int32_t csgd_batch_create(csgd_solver* const* solvers, const int64_t* n_steps,
+                          float* const* x_out, int32_t n, const csgd_batch_params* params,
+                          csgd_batch** out);
+/* Enqueues the batch's graph on the stream (asynchronous). */
+int32_t csgd_batch_launch(csgd_batch* batch, csgd_stream stream);
+/* Waits for the batch's last launch; CSGD_ERR_TIMEOUT if one of its waits ran
+ * out (the solvers' states are then undefined), CSGD_OK otherwise. */
+int32_t csgd_batch_status(csgd_batch* batch);
+/* Tasks, blocks of work and executor blocks of the batch (for reports). */
+int32_t csgd_batch_info(csgd_batch* batch, int32_t* n_tasks, int64_t* n_units, int32_t* grid);
+int32_t csgd_batch_destroy(csgd_batch* batch);
+
 /* Launch shapes (the paper has no counterpart: these tune the GPU kernels, not
  * the method).  bp_groups = view groups per backprojection CTA (1..8) of the
- * voxel-driven gather, or -1 for the ray-driven scatter backprojection (each
- * ray walks the tile and adds len * r to 64-bit fixed-point sums with integer
- * atomics: exact and order-independent, so also deterministic); fwd_lanes =
+ * voxel-driven gather, -1 for the ray-driven scatter backprojection (each
+ * ray walks the tile and adds len * r to 32-bit fixed-point sums with integer
+ * atomics: exact and order-independent, so also deterministic), or -2, -3, -4
+ * for the brick backprojection with brick shape 0, 1, 2 (3D bricks of 16 x 16
+ * x 16, 8 or 4 voxels, 2D bricks of 32^2, 16^2 or 8^2: a block per brick walks
+ * the lines that cross it and sums in shared-memory fixed point); fwd_lanes =
  * lanes per ray of the dual forward and of the scatter (1, 2 or 4); 0 selects
  * the library's model (gather, occupancy-based groups, lanes by ray count).
  * They change only the rounding of the sums, i.e. results at rounding level.

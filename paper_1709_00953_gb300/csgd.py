@@ -86,6 +86,11 @@ class Report(ctypes.Structure):
                 ("rays", ctypes.c_int64), ("tile_voxels", ctypes.c_int64)]
 
 
+class BatchParams(ctypes.Structure):
+    _fields_ = [("wait_limit_ns", ctypes.c_int64), ("stall_last_task", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 # every symbol include/csgd.h declares, with its signature
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
@@ -120,6 +125,12 @@ SIGNATURES = {
     "csgd_graph_batch_create": ([ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp)], _i32),
     "csgd_graph_launch": ([_vp, _vp], _i32),
     "csgd_graph_destroy": ([_vp], _i32),
+    "csgd_batch_create": ([ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(_vp), _i32,
+                           ctypes.POINTER(BatchParams), ctypes.POINTER(_vp)], _i32),
+    "csgd_batch_launch": ([_vp, _vp], _i32),
+    "csgd_batch_status": ([_vp], _i32),
+    "csgd_batch_info": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i32)], _i32),
+    "csgd_batch_destroy": ([_vp], _i32),
     "csgd_solver_profile": ([_vp, _i32], _i32),
     "csgd_solver_profile_read": ([_vp, ctypes.POINTER(KernelTimes), _i32], _i32),
     "csgd_last_error": ([], ctypes.c_char_p),
@@ -487,6 +498,47 @@ def graph_batch(graphs) -> Graph:
     h = ctypes.c_void_p()
     _check(load().csgd_graph_batch_create(arr, len(graphs), ctypes.byref(h)))
     return Graph(h, list(graphs))
+
+
+class Batch:
+    """Many solves in one persistent launch with a device work queue
+    (csgd_batch_create): solvers[k] runs n_steps[k] steps from its seed and
+    writes x to x_out[k] (CUDA float32, or None)."""
+
+    def __init__(self, solvers, n_steps, x_out=None, wait_limit_ns: int = 0,
+                 stall_last_task: bool = False):
+        n = len(solvers)
+        outs = list(x_out) if x_out is not None else [None] * n
+        hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+        st = (ctypes.c_int64 * n)(*[int(k) for k in n_steps])
+        xs = (ctypes.c_void_p * n)(*[(_dev_ptr(x, "x_out", sv.part.n_voxels).value if x is not None
+                                      else None) for x, sv in zip(outs, solvers)])
+        prm = BatchParams(int(wait_limit_ns), int(bool(stall_last_task)), 0)
+        h = ctypes.c_void_p()
+        _check(load().csgd_batch_create(hs, st, xs, n, ctypes.byref(prm), ctypes.byref(h)))
+        self.handle = h
+        self._keep = [solvers, outs]
+
+    def launch(self, stream=None):
+        _check(load().csgd_batch_launch(self.handle, _stream(stream)))
+
+    def status(self):
+        """Waits for the last launch; raises CsgdError (CSGD_ERR_TIMEOUT) if a wait ran out."""
+        _check(load().csgd_batch_status(self.handle))
+
+    def info(self) -> dict:
+        nt, gr, nu = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(load().csgd_batch_info(self.handle, ctypes.byref(nt), ctypes.byref(nu), ctypes.byref(gr)))
+        return dict(tasks=nt.value, units=nu.value, blocks=gr.value)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.csgd_batch_destroy(self.handle)
+            self.handle = None
+
+
+def batch_create(solvers, n_steps, x_out=None, **kw) -> Batch:
+    return Batch(solvers, n_steps, x_out, **kw)
 
 
 def solver_create(part: Partition, params: dict, y, stream=None) -> Solver:

@@ -1198,6 +1198,159 @@ int32_t csgd_graph_batch_create(csgd_graph* const* parts, int32_t n, csgd_graph*
     return CSGD_OK;
 }
 
+struct csgd_batch {
+    ExecPlan* plan = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    int device = 0;
+};
+
+int32_t csgd_batch_destroy(csgd_batch* B) {
+    if (!B) return CSGD_OK;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->done) cudaEventDestroy(B->done);
+    exec_plan_free(B->plan);
+    delete B;
+    return CSGD_OK;
+}
+
+int32_t csgd_batch_create(csgd_solver* const* solvers, const int64_t* n_steps, float* const* x_out,
+                          int32_t n, const csgd_batch_params* params, csgd_batch** out) {
+    if (!solvers || !n_steps || n < 1 || !out) return fail(CSGD_ERR_INVALID_ARG, "bad argument");
+    *out = nullptr;
+    int dev = 0;
+    CSGD_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    int dim = 0;
+    for (int k = 0; k < n; ++k) {
+        csgd_solver* S = solvers[k];
+        if (!S || n_steps[k] < 0) return fail(CSGD_ERR_INVALID_ARG, "NULL solver or negative steps");
+        if (S->profiling) return fail(CSGD_ERR_STATE, "disable profiling before building a batch");
+        if (S->P->p.device != dev) return fail(CSGD_ERR_INVALID_ARG, "solvers on another device");
+        if (dim && S->P->p.dg.dim != dim) return fail(CSGD_ERR_INVALID_ARG, "mixed 2D and 3D solvers");
+        dim = S->P->p.dg.dim;
+        for (int m = 0; m < k; ++m)
+            if (solvers[m] == S) return fail(CSGD_ERR_INVALID_ARG, "a solver appears twice");
+    }
+    csgd_batch* B = new (std::nothrow) csgd_batch;
+    if (!B) return fail(CSGD_ERR_OOM, "host allocation");
+    B->device = dev;
+    B->plan = exec_plan_new(n);
+    if (!B->plan) {
+        delete B;
+        return fail(CSGD_ERR_OOM, "host allocation");
+    }
+    cudaStream_t cs = nullptr;
+    int rc = CSGD_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamCreate");
+    // plan every solve from a fresh schedule, upload it, and turn its kernels
+    // into executor tasks
+    for (int k = 0; rc == CSGD_OK && k < n; ++k) {
+        csgd_solver* S = solvers[k];
+        const Partition& p = S->P->p;
+        solver_reset_host(S);
+        Plan pl;
+        plan_scheduled(S, &pl, n_steps[k], true);
+        rc = prepare_plan(S, pl, cs);
+        for (const auto& op : pl.ops) {
+            if (rc) break;
+            if (op.n < 0) {
+                exec_plan_add_close(B->plan, k, p.dg, S->sb, S->n_rays, p.max_tile_voxels,
+                                    S->prm.sync == CSGD_SYNC_EPOCH);
+                continue;
+            }
+            BatchLaunch b;
+            b.first = op.first;
+            b.nslots = op.n;
+            b.j = op.j;
+            b.max_rays = op.max_rays;
+            b.w_begin = pl.steps[op.first].w0;
+            b.n_items = pl.steps[op.first + op.n - 1].w1 - b.w_begin;
+            b.max_item_rays = 0;
+            for (int w = b.w_begin; w < b.w_begin + b.n_items; ++w)
+                b.max_item_rays = std::max<int64_t>(
+                    b.max_item_rays,
+                    (int64_t)(pl.items[w].u1 - pl.items[w].u0) * (pl.items[w].v1 - pl.items[w].v0));
+            b.sync_epoch = S->prm.sync == CSGD_SYNC_EPOCH;
+            b.bp_groups = S->bp_groups;
+            b.fwd_lanes = 1;
+            e = exec_plan_add_batch(B->plan, k, p.dg, p.tiles_h[op.j], S->d_items, S->d_steps, b, S->sb,
+                                    S->P->sm_count);
+            if (e != cudaSuccess) rc = cuda_fail(e, "batch task");
+        }
+        if (rc == CSGD_OK && x_out && x_out[k])
+            exec_plan_add_xout(B->plan, k, p.dg, S->sb.x, x_out[k], p.max_tile_voxels);
+        solver_reset_host(S);  // every launch starts from the seed; so does the host side
+    }
+    if (rc == CSGD_OK) {
+        const int64_t wait = params && params->wait_limit_ns > 0 ? params->wait_limit_ns
+                                                                  : (int64_t)2000000000;
+        e = exec_plan_finalize(B->plan, wait, params ? params->stall_last_task : 0,
+                               solvers[0]->P->sm_count);
+        if (e != cudaSuccess) rc = cuda_fail(e, "batch plan upload");
+    }
+    if (rc == CSGD_OK) {
+        e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) rc = cuda_fail(e, "upload sync");
+    }
+    // the graph: every solver's reset, then the persistent launch
+    if (rc == CSGD_OK) {
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) rc = cuda_fail(e, "begin capture");
+        for (int k = 0; rc == CSGD_OK && k < n; ++k) rc = solver_reset_device(solvers[k], cs);
+        if (rc == CSGD_OK) {
+            e = exec_plan_launch(B->plan, cs);
+            if (e != cudaSuccess) rc = cuda_fail(e, "executor launch");
+        }
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cs, &g);
+        if (rc == CSGD_OK && e != cudaSuccess) rc = cuda_fail(e, "end capture");
+        B->graph = g;
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (rc == CSGD_OK) {
+        e = cudaGraphInstantiate(&B->exec, B->graph, 0);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->done, cudaEventDisableTiming);
+        if (e != cudaSuccess) rc = cuda_fail(e, "graph instantiate");
+    }
+    if (rc) {
+        std::string m = g_err;
+        csgd_batch_destroy(B);
+        return fail(rc, m);
+    }
+    *out = B;
+    return CSGD_OK;
+}
+
+int32_t csgd_batch_launch(csgd_batch* B, csgd_stream stream) {
+    if (!B) return fail(CSGD_ERR_INVALID_ARG, "NULL batch");
+    CSGD_CUDA(cudaGraphLaunch(B->exec, (cudaStream_t)stream), "batch launch");
+    CSGD_CUDA(cudaEventRecord(B->done, (cudaStream_t)stream), "batch event");
+    return CSGD_OK;
+}
+
+int32_t csgd_batch_status(csgd_batch* B) {
+    if (!B) return fail(CSGD_ERR_INVALID_ARG, "NULL batch");
+    CSGD_CUDA(cudaEventSynchronize(B->done), "batch sync");
+    int st = 0;
+    CSGD_CUDA(exec_plan_status(B->plan, &st), "batch status");
+    if (st) return fail(CSGD_ERR_TIMEOUT, "a wait of the batch executor ran out of time");
+    return CSGD_OK;
+}
+
+int32_t csgd_batch_info(csgd_batch* B, int32_t* n_tasks, int64_t* n_units, int32_t* grid) {
+    if (!B || !n_tasks || !n_units || !grid) return fail(CSGD_ERR_INVALID_ARG, "NULL argument");
+    int nt = 0, gr = 0;
+    int64_t nu = 0;
+    exec_plan_info(B->plan, &nt, &nu, &gr);
+    *n_tasks = nt;
+    *n_units = nu;
+    *grid = gr;
+    return CSGD_OK;
+}
+
 int32_t csgd_graph_launch(csgd_graph* G, csgd_stream stream) {
     if (!G || !G->exec) return fail(CSGD_ERR_INVALID_ARG, "NULL graph");
     CSGD_CUDA(cudaGraphLaunch(G->exec, (cudaStream_t)stream), "cudaGraphLaunch");

@@ -25,7 +25,11 @@
 // stream serialization (see pdl_wait in device.cuh).
 #include <cuda_runtime.h>
 
+#include <string.h>
+
 #include <algorithm>
+#include <new>
+#include <vector>
 #include <mutex>
 #include <utility>
 
@@ -37,6 +41,28 @@ namespace csgd {
 namespace {
 
 constexpr int kFwdBatch = 4;  // crossings per batch of gathers in the dual forward
+constexpr int kMaxBlock = 256;  // most threads of any CTA of the solver's kernels
+
+// Index of a thread block in its grid as the kernel bodies see it: blockIdx and
+// gridDim for an ordinary launch; for the batch executor (one persistent
+// launch running many kernels' blocks) the block of the unit it runs.
+struct VBlock {
+    unsigned x, y, z;     // block index
+    unsigned gx, gy, gz;  // grid size
+};
+__device__ __forceinline__ VBlock hw_block() {
+    return VBlock{blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z};
+}
+
+// Load of data an earlier kernel of the stream wrote: through the read-only
+// cache in an ordinary launch (written before the kernel started); a plain
+// load inside the executor, where the writer may be another block of the same
+// launch (ordered by the executor's acquire, which the read-only path is not).
+template <bool EX, class T>
+__device__ __forceinline__ T ldro(const T* p) {
+    if constexpr (EX) return *p;
+    else return __ldg(p);
+}
 constexpr int kBPMaxThreads = kBPVox * kBPMaxChunks;
 constexpr int kEpiThreads = 256;
 
@@ -160,16 +186,16 @@ __global__ void __launch_bounds__(kFwdThreads) k_project_inline(
 // writes its partial sum of squares (FP32); the last CTA of the slot to finish
 // adds them in a fixed order (exactly as FP32 pairs, then in FP64) and computes
 // mu = beta g^T g / q^T q (no grid barrier).
-template <int DIM, int L, bool TABLE>
-__global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
+template <int DIM, int L, bool TABLE, bool EX>
+__device__ __forceinline__ void forward_dual_body(const FwdSolverArgs& a, const VBlock& vb) {
     pdl_trigger();
     const DevGeom& G = a.G;
-    const int slot = blockIdx.y;
+    const int slot = vb.y;
     const StepDesc sd = a.steps[a.first + slot];
     const DevTile t = G.tiles[sd.j];
     const int nvox = t.n[0] * t.n[1] * t.n[2];
     const int lane = threadIdx.x & 31;
-    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t gid = (int64_t)vb.x * blockDim.x + threadIdx.x;
     int64_t k = gid / L;
     const int sub = (int)(gid % L);
     const bool active = k < sd.n_rays;
@@ -225,7 +251,7 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
 #pragma unroll
                 for (int u = 0; u < kFwdBatch; ++u)
                     e[u] = ln[u] > 0.f && (unsigned)id[u] < (unsigned)nvox
-                               ? __ldg(xg + id[u]) : make_float2(0.f, 0.f);
+                               ? ldro<EX>(xg + id[u]) : make_float2(0.f, 0.f);
                 float px[kFwdBatch], py[kFwdBatch];
 #pragma unroll
                 for (int u = 0; u < kFwdBatch; ++u) {
@@ -260,19 +286,19 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     // per-CTA partials in FP32 (the squares, a warp tree, then the warps in
     // order: within 9 u of the CTA's exact sum of squares), then the last CTA
     // of the slot to finish adds the partials in a fixed order
-    __shared__ double s_q[kFwdThreads / 32];
-    __shared__ float s_qf[kFwdThreads / 32];
+    __shared__ double s_q[kMaxBlock / 32];
+    __shared__ float s_qf[kMaxBlock / 32];
     __shared__ unsigned s_last;
     const float wq = warp_sum_f(qq);
     if (lane == 0) s_qf[threadIdx.x >> 5] = wq;
     __syncthreads();
     if (threadIdx.x == 0) {
         float cq = 0.f;
-        for (int w = 0; w < kFwdThreads / 32; ++w) cq += s_qf[w];
-        a.sb.qq_part[(int64_t)slot * a.sb.qq_stride + blockIdx.x] = cq;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) cq += s_qf[w];
+        a.sb.qq_part[(int64_t)slot * a.sb.qq_stride + vb.x] = cq;
         __threadfence();
         const unsigned prev = atomicAdd(a.sb.counters + slot, 1u);
-        s_last = prev == gridDim.x - 1;
+        s_last = prev == vb.gx - 1;
     }
     __syncthreads();
     if (!s_last) return;
@@ -280,7 +306,7 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     // thread t adds partials t, t + blockDim.x, ... in order, error-free in
     // FP32 pairs; then a fixed FP64 tree over the threads
     TwoSumF tq, tg;
-    for (int w = threadIdx.x; w < (int)gridDim.x; w += blockDim.x)
+    for (int w = threadIdx.x; w < (int)vb.gx; w += blockDim.x)
         tq.add(__ldcg(a.sb.qq_part + (int64_t)slot * a.sb.qq_stride + w));
     for (int w = threadIdx.x; w < a.n_gg; w += blockDim.x)
         tg.add(__ldcg(a.sb.gg_part + (int64_t)slot * a.sb.gg_stride + w));
@@ -306,6 +332,11 @@ __global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
     }
 }
 
+template <int DIM, int L, bool TABLE>
+__global__ void __maxnreg__(64) k_forward_dual(const FwdSolverArgs a) {
+    forward_dual_body<DIM, L, TABLE, false>(a, hw_block());
+}
+
 // ---------------------------------------------------------------------------
 // backprojection
 // ---------------------------------------------------------------------------
@@ -326,8 +357,9 @@ struct TableArgs {
 // records written after it.
 constexpr int kTablePre = 4;
 
-template <int DIM>
-__device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkItem& it) {
+template <int DIM, bool EX>
+__device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkItem& it,
+                                               const VBlock& vb) {
     const DevGeom& G = a.G;
     const DevView V = G.views[it.view];
     const DevVT E = G.vt[(int64_t)it.view * G.n_tiles + a.j];
@@ -335,8 +367,8 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
     const int wu = it.u1 - it.u0;
     const int nr = wu * (it.v1 - it.v0);
     RayRec* dst = a.table + (int64_t)it.slot * a.slot_stride + it.ray_off;
-    const int k0 = blockIdx.y * blockDim.x + threadIdx.x;
-    const int stride = gridDim.y * blockDim.x;
+    const int k0 = vb.y * blockDim.x + threadIdx.x;
+    const int stride = vb.gy * blockDim.x;
     float pq[kTablePre][3], pi[kTablePre][3];
 #pragma unroll
     for (int p = 0; p < kTablePre; ++p) {
@@ -350,7 +382,7 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
         const int k = k0 + p * stride;
         if (k < nr) {
             const int64_t ray = ray_index(G, it.view, it.u0 + k % wu, it.v0 + k / wu);
-            const float rv = __ldg(a.r + ray);
+            const float rv = ldro<EX>(a.r + ray);
             *reinterpret_cast<float4*>(dst[k].a) = make_float4(pq[p][0], pq[p][1], pi[p][0], pi[p][1]);
             *reinterpret_cast<float4*>(dst[k].b) =
                 make_float4(rv, pq[p][2], pi[p][2], __int_as_float((int)ray));
@@ -362,7 +394,7 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
         float q[3], inv[3];
         table_ray<DIM>(G, it.view, V, E, tile, ku, kv, q, inv);
         const int64_t ray = ray_index(G, it.view, ku, kv);
-        const float rv = __ldg(a.r + ray);
+        const float rv = ldro<EX>(a.r + ray);
         *reinterpret_cast<float4*>(dst[k].a) = make_float4(q[0], q[1], inv[0], inv[1]);
         *reinterpret_cast<float4*>(dst[k].b) =
             make_float4(rv, q[2], inv[2], __int_as_float((int)ray));
@@ -372,33 +404,44 @@ __device__ __forceinline__ void ray_table_item(const TableArgs& a, const WorkIte
 template <int DIM>
 __global__ void __launch_bounds__(256) k_ray_table_inline(const TableArgs a,
                                                           const __grid_constant__ InlineItems it) {
-    ray_table_item<DIM>(a, it.items[blockIdx.x]);
+    ray_table_item<DIM, false>(a, it.items[blockIdx.x], hw_block());
+}
+
+template <int DIM, bool EX>
+__device__ __forceinline__ void ray_table_body(const TableArgs& a, const WorkItem* items,
+                                               const VBlock& vb) {
+    pdl_trigger();
+    const WorkItem it = items[a.w_begin + vb.x];
+    ray_table_item<DIM, EX>(a, it, vb);
 }
 
 template <int DIM>
 __global__ void __launch_bounds__(256) k_ray_table_solver(const TableArgs a,
                                                           const WorkItem* __restrict__ items) {
-    pdl_trigger();
-    const WorkItem it = items[a.w_begin + blockIdx.x];
-    ray_table_item<DIM>(a, it);
+    ray_table_body<DIM, false>(a, items, hw_block());
 }
 
 // max |r| per slot over the rays of the batch's work items (the scatter's
 // fixed-point scale when it sets its lines up itself): one CTA row per item.
-__global__ void __launch_bounds__(256) k_slot_rmax(const TableArgs a,
-                                                   const WorkItem* __restrict__ items) {
+__device__ __forceinline__ void slot_rmax_body(const TableArgs& a, const WorkItem* items,
+                                               const VBlock& vb) {
     pdl_trigger();
-    const WorkItem it = items[a.w_begin + blockIdx.x];
+    const WorkItem it = items[a.w_begin + vb.x];
     const DevGeom& G = a.G;
     const int wu = it.u1 - it.u0;
     const int nr = wu * (it.v1 - it.v0);
     pdl_wait();  // r belongs to earlier kernels until here
     float rm = 0.f;
-    for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < nr; k += gridDim.y * blockDim.x)
+    for (int k = vb.y * blockDim.x + threadIdx.x; k < nr; k += vb.gy * blockDim.x)
         rm = fmaxf(rm, fabsf(a.r[ray_index(G, it.view, it.u0 + k % wu, it.v0 + k / wu)]));
     // non-negative floats order like their bit patterns
     const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(rm));
     if ((threadIdx.x & 31) == 0 && wm) atomicMax(a.rmax + it.slot, wm);
+}
+
+__global__ void __launch_bounds__(256) k_slot_rmax(const TableArgs a,
+                                                   const WorkItem* __restrict__ items) {
+    slot_rmax_body(a, items, hw_block());
 }
 
 struct BPArgs {
@@ -713,7 +756,7 @@ __device__ __forceinline__ float view_sum(const DevGeom&, const ViewCtx3& c, con
 // order.  C is chosen per launch so that the grid fills whole waves.
 template <int DIM>
 __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem* items,
-                                                 const StepDesc& sd, int slot) {
+                                                 const StepDesc& sd, int slot, unsigned patch) {
     using Ctx = typename ViewCtxOf<DIM>::type;
     __shared__ float part[kBPMaxThreads];
     __shared__ Ctx vs[kViewBatch];
@@ -726,7 +769,7 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
     // thread's voxel in it: a compact patch shares candidate rays among its voxels
     constexpr int P0 = DIM == 2 ? 8 : 4, P1 = DIM == 2 ? 8 : 4;
     const int nb0 = (t.n[0] + P0 - 1) / P0, nb1 = (t.n[1] + P1 - 1) / P1;
-    const int b0 = blockIdx.x % nb0, b12 = blockIdx.x / nb0;
+    const int b0 = patch % nb0, b12 = patch / nb0;
     const int x0 = b0 * P0 + lv % P0;
     const int x1 = (b12 % nb1) * P1 + (lv / P0) % P1;
     const int x2 = DIM == 3 ? (b12 / nb1) * 4 + lv / (P0 * P1) : 0;
@@ -817,7 +860,7 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
         if (a.gg_part) {
             float cg = 0.f;
             for (int k = 0; k < nw; ++k) cg += s_gg[k];
-            a.gg_part[(int64_t)slot * a.gg_stride + blockIdx.x] = cg;
+            a.gg_part[(int64_t)slot * a.gg_stride + patch] = cg;
         }
         if (a.nnz_slot) {
             unsigned long long cn = 0;
@@ -830,15 +873,21 @@ __device__ __forceinline__ void backproject_body(const BPArgs& a, const WorkItem
 template <int DIM>
 __global__ void __maxnreg__(64) k_backproject_inline(
     const BPArgs a, const __grid_constant__ InlineItems it) {
-    backproject_body<DIM>(a, it.items, it.step, 0);
+    backproject_body<DIM>(a, it.items, it.step, 0, blockIdx.x);
+}
+
+template <int DIM>
+__device__ __forceinline__ void backproject_solver_body(const BPArgs& a, const WorkItem* items,
+                                                        const StepDesc* steps, const VBlock& vb) {
+    pdl_trigger();
+    const StepDesc sd = steps[a.first + vb.z];
+    backproject_body<DIM>(a, items, sd, vb.z, vb.x);
 }
 
 template <int DIM>
 __global__ void __maxnreg__(64) k_backproject_solver(
     const BPArgs a, const WorkItem* __restrict__ items, const StepDesc* __restrict__ steps) {
-    pdl_trigger();
-    const StepDesc sd = steps[a.first + blockIdx.z];
-    backproject_body<DIM>(a, items, sd, blockIdx.z);
+    backproject_solver_body<DIM>(a, items, steps, hw_block());
 }
 
 // ---------------------------------------------------------------------------
@@ -880,14 +929,14 @@ __device__ __forceinline__ int scatter_shift(unsigned rmax_bits, float terms) {
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
 
 template <int DIM, int L>
-__global__ void __maxnreg__(64) k_backproject_scatter(const ScatterArgs a) {
+__device__ __forceinline__ void scatter_body(const ScatterArgs& a, const VBlock& vb) {
     pdl_trigger();
     const DevGeom& G = a.G;
-    const int slot = blockIdx.y;
+    const int slot = vb.y;
     const StepDesc sd = a.steps[a.first + slot];
     const DevTile t = G.tiles[sd.j];
     const int nvox = t.n[0] * t.n[1] * t.n[2];
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gid = (int64_t)vb.x * blockDim.x + threadIdx.x;
     const int64_t k = gid / L;
     const int sub = (int)(gid % L);
     const bool active = k < sd.n_rays;
@@ -942,16 +991,21 @@ __global__ void __maxnreg__(64) k_backproject_scatter(const ScatterArgs a) {
         if (sub > 0 && first_id >= 0 && first_id == prev_last) --nz;
     }
     if (a.sb.nnz_slot) {
-        __shared__ unsigned s_nz[kFwdThreads / 32];
+        __shared__ unsigned s_nz[kMaxBlock / 32];
         const unsigned wn = __reduce_add_sync(0xffffffffu, (unsigned)nz);
         if ((threadIdx.x & 31) == 0) s_nz[threadIdx.x >> 5] = wn;
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned long long cn = 0;
-            for (int w = 0; w < kFwdThreads / 32; ++w) cn += s_nz[w];
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) cn += s_nz[w];
             if (cn) atomicAdd(a.sb.nnz_slot + slot, cn);
         }
     }
+}
+
+template <int DIM, int L>
+__global__ void __maxnreg__(64) k_backproject_scatter(const ScatterArgs a) {
+    scatter_body<DIM, L>(a, hw_block());
 }
 
 constexpr int kConvThreads = 256;
@@ -959,10 +1013,10 @@ constexpr int kConvThreads = 256;
 // g_J = h 2^-S acc (one rounding from the exact fixed-point sum), the pairs
 // (x_J, g_J) for the dual forward, a g^T g partial per CTA (FP32 as in the
 // gather), and acc cleared for the next batch.
-__global__ void __launch_bounds__(kConvThreads) k_scatter_convert(const ScatterArgs a) {
+__device__ __forceinline__ void scatter_convert_body(const ScatterArgs& a, const VBlock& vb) {
     pdl_trigger();
     const DevGeom& G = a.G;
-    const int slot = blockIdx.y;
+    const int slot = vb.y;
     const StepDesc sd = a.steps[a.first + slot];
     const DevTile t = G.tiles[sd.j];
     const int nvox = t.n[0] * t.n[1] * t.n[2];
@@ -973,22 +1027,26 @@ __global__ void __launch_bounds__(kConvThreads) k_scatter_convert(const ScatterA
     float2* gout = reinterpret_cast<float2*>(a.sb.g) + (int64_t)slot * a.sb.g_stride;
     const float* xt = a.sb.x + t.voff;
     float gg = 0.f;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += gridDim.x * blockDim.x) {
-        const int s = acc[v];
+    for (int v = vb.x * blockDim.x + threadIdx.x; v < nvox; v += vb.gx * blockDim.x) {
+        const int s = __ldcg(acc + v);  // summed by L2 atomics
         acc[v] = 0;
         const float g = (float)s * isc * G.h;
         gout[v] = make_float2(xt[v], g);
         gg = fmaf(g, g, gg);
     }
-    __shared__ float s_gg[kConvThreads / 32];
+    __shared__ float s_gg[kMaxBlock / 32];
     const float wg = warp_sum_f(gg);
     if ((threadIdx.x & 31) == 0) s_gg[threadIdx.x >> 5] = wg;
     __syncthreads();
     if (threadIdx.x == 0) {
         float cg = 0.f;
-        for (int w = 0; w < kConvThreads / 32; ++w) cg += s_gg[w];
-        a.sb.gg_part[(int64_t)slot * a.sb.gg_stride + blockIdx.x] = cg;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) cg += s_gg[w];
+        a.sb.gg_part[(int64_t)slot * a.sb.gg_stride + vb.x] = cg;
     }
+}
+
+__global__ void __launch_bounds__(kConvThreads) k_scatter_convert(const ScatterArgs a) {
+    scatter_convert_body(a, hw_block());
 }
 
 // ---------------------------------------------------------------------------
@@ -1298,13 +1356,13 @@ struct EpiArgs {
 // remaining CTAs add the batch's candidates into x^ of the tile.
 constexpr int kEpiMu = 32;
 
-__global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
+__device__ __forceinline__ void epilogue_body(const EpiArgs& a, const VBlock& vb) {
     pdl_trigger();
     const DevGeom& G = a.G;
-    if ((int)blockIdx.x < a.n_items) {
+    if ((int)vb.x < a.n_items) {
         // the item and its (view, tile) constants are fixed for the solve: read
         // them before waiting for the dual forward
-        const WorkItem it = a.items[a.w_begin + blockIdx.x];
+        const WorkItem it = a.items[a.w_begin + vb.x];
         const DevVT& E = G.vt[(int64_t)it.view * G.n_tiles + a.j];
         const int ew = E.u1 - E.u0;
         const int64_t zbase = E.zoff - (int64_t)E.v0 * ew - E.u0;
@@ -1312,7 +1370,7 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
         const int nr = wu * (it.v1 - it.v0);
         pdl_wait();
         const float mu = (float)a.sb.mu[it.slot];
-        for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < nr; k += gridDim.y * blockDim.x) {
+        for (int k = vb.y * blockDim.x + threadIdx.x; k < nr; k += vb.gy * blockDim.x) {
             const int ku = it.u0 + k % wu;
             const int kv = it.v0 + k / wu;
             const int64_t zi = zbase + (int64_t)kv * ew + ku;
@@ -1332,8 +1390,8 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
         pdl_wait();
         float* xh = a.sb.xh + t.voff;
         const float* x = a.sb.x + t.voff;
-        const int64_t nthreads = (int64_t)(gridDim.x - a.n_items) * gridDim.y * blockDim.x;
-        int64_t v0 = ((int64_t)(blockIdx.x - a.n_items) * gridDim.y + blockIdx.y) * blockDim.x +
+        const int64_t nthreads = (int64_t)(vb.gx - a.n_items) * vb.gy * blockDim.x;
+        int64_t v0 = ((int64_t)(vb.x - a.n_items) * vb.gy + vb.y) * blockDim.x +
                      threadIdx.x;
         // the step lengths of the first kEpiMu slots converted once per CTA,
         // not once per voxel
@@ -1350,23 +1408,28 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
                 s += fmaf((float)a.sb.mu[sl], a.sb.g[2 * ((int64_t)sl * a.sb.g_stride + v) + 1], xv);
             xh[v] = s;
         }
-        if (blockIdx.x == a.n_items && blockIdx.y == 0 && threadIdx.x == 0)
+        if (vb.x == a.n_items && vb.y == 0 && threadIdx.x == 0)
             a.sb.cnt[a.j] += a.nslots;
     }
 }
 
+__global__ void __launch_bounds__(kEpiThreads) k_epilogue(const EpiArgs a) {
+    epilogue_body(a, hw_block());
+}
+
 // x_J = x^_J / count_J and x^_J = 0 for every tile (grid.y = tile), 16-byte
 // accesses over the aligned body of each tile's range.
-__global__ void k_average(const DevGeom G, float* x, float* xh, const int32_t* cnt) {
+__device__ __forceinline__ void average_body(const DevGeom& G, float* x, float* xh,
+                                             const int32_t* cnt, const VBlock& vb) {
     pdl_trigger();
     pdl_wait();
-    const int j = blockIdx.y;
+    const int j = vb.y;
     const DevTile t = G.tiles[j];
     const int64_t a0 = t.voff, a1 = t.voff + (int64_t)t.n[0] * t.n[1] * t.n[2];
     const int64_t b0 = min(a1, (a0 + 3) & ~(int64_t)3), b1 = max(b0, a1 & ~(int64_t)3);
     const int c = cnt[j];
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)vb.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)vb.gx * blockDim.x;
     auto one = [&](int64_t v) {
         if (c > 0) x[v] = xh[v] / (float)c;
         xh[v] = 0.f;
@@ -1383,11 +1446,16 @@ __global__ void k_average(const DevGeom G, float* x, float* xh, const int32_t* c
     }
 }
 
-__global__ void k_apply_pending(float* r, float* d, int64_t n) {
+__global__ void k_average(const DevGeom G, float* x, float* xh, const int32_t* cnt) {
+    average_body(G, x, xh, cnt, hw_block());
+}
+
+__device__ __forceinline__ void apply_pending_body(float* r, float* d, int64_t n,
+                                                   const VBlock& vb) {
     pdl_trigger();
     pdl_wait();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)vb.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)vb.gx * blockDim.x) {
         float dv = d[i];
         if (dv != 0.f) {
             r[i] -= dv;
@@ -1396,12 +1464,17 @@ __global__ void k_apply_pending(float* r, float* d, int64_t n) {
     }
 }
 
-__global__ void k_tile_to_rowmajor(const DevGeom G, const float* xt, float* out) {
-    const int j = blockIdx.y;
+__global__ void k_apply_pending(float* r, float* d, int64_t n) {
+    apply_pending_body(r, d, n, hw_block());
+}
+
+__device__ __forceinline__ void tile_to_rowmajor_body(const DevGeom& G, const float* xt,
+                                                      float* out, const VBlock& vb) {
+    const int j = vb.y;
     const DevTile t = G.tiles[j];
     const int64_t nv = (int64_t)t.n[0] * t.n[1] * t.n[2];
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv;
-         v += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t v = (int64_t)vb.x * blockDim.x + threadIdx.x; v < nv;
+         v += (int64_t)vb.gx * blockDim.x) {
         int x0 = (int)(v % t.n[0]);
         int64_t rest = v / t.n[0];
         int x1 = (int)(rest % t.n[1]);
@@ -1409,6 +1482,10 @@ __global__ void k_tile_to_rowmajor(const DevGeom G, const float* xt, float* out)
         int64_t gi = ((int64_t)(t.lo[2] + x2) * G.ny + t.lo[1] + x1) * G.nx + t.lo[0] + x0;
         out[gi] = xt[t.voff + v];
     }
+}
+
+__global__ void k_tile_to_rowmajor(const DevGeom G, const float* xt, float* out) {
+    tile_to_rowmajor_body(G, xt, out, hw_block());
 }
 
 __global__ void k_sq_residual(const float* y, const float* ax, int64_t n, double* out) {
@@ -1423,6 +1500,196 @@ __global__ void k_sq_residual(const float* y, const float* ax, int64_t n, double
     if (threadIdx.x == 0) out[blockIdx.x] = b;
 }
 
+
+// ---------------------------------------------------------------------------
+// Batch executor: one persistent launch that runs the kernels of many solves.
+//
+// The host lists, per problem, the kernels its solve would launch (ray table or
+// max |r| pass, backprojection, conversion, dual forward, epilogue, epoch
+// closes, x out) as tasks of `units` thread blocks each, and interleaves the
+// problems' lists round-robin.  A block of the executor takes the next unit
+// from a device ticket counter, waits until every unit of its problem's
+// earlier tasks has completed (a per-problem counter of completed units, read
+// with acquire semantics), runs the unit with the task's kernel body and its
+// virtual block index, and counts it as completed (release).  Tickets are
+// handed out in list order and a unit only waits for units of smaller tickets,
+// so the smallest outstanding unit can always run: no deadlock.  Every wait is
+// bounded (wait_ns of GPU time); a wait that runs out sets the status word, and
+// every block stops taking work once it is set.
+// ---------------------------------------------------------------------------
+enum ExecKind : int32_t {
+    kExTable2, kExTable3, kExRmax, kExGather2, kExGather3, kExScatter2, kExScatter3, kExConvert,
+    kExFwdTable2, kExFwdTable3, kExFwdInline2, kExFwdInline3, kExEpilogue, kExApply, kExAverage,
+    kExClear, kExXout
+};
+
+struct ExecMisc {
+    DevGeom G;
+    float* x;
+    float* xh;
+    int32_t* cnt;
+    float* r;
+    float* d;
+    int64_t n;
+    const float* xt;
+    float* out;
+};
+
+struct ExecTask {
+    int32_t kind;
+    int32_t problem;
+    uint32_t gx, gy, gz;
+    uint32_t units;
+    uint32_t dep;  // completed units of the problem that must precede this task
+    uint32_t pad;
+    const WorkItem* items;
+    const StepDesc* steps;
+    union {
+        TableArgs table;
+        BPArgs bp;
+        ScatterArgs sc;
+        FwdSolverArgs fwd;
+        EpiArgs epi;
+        ExecMisc misc;
+    } a;
+};
+
+struct ExecArgs {
+    const ExecTask* tasks;
+    const unsigned long long* prefix;  // [n_tasks + 1]: units of the tasks before
+    int n_tasks;
+    unsigned long long n_units;
+    unsigned long long* ticket;
+    unsigned* done;  // [problem]: completed units
+    int* status;     // 0, or 1 once a wait ran out
+    long long wait_ns;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+
+__device__ __forceinline__ void clear_counts_body(int32_t* cnt, int n) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) cnt[k] = 0;
+}
+
+// One wrapper per task kind, not inlined: each kernel body keeps its own
+// register allocation inside the executor.
+#define CSGD_EXEC_WRAP(name, call)                                                     \
+    __device__ __noinline__ void name(const ExecTask& T, const VBlock& vb) { call; }
+CSGD_EXEC_WRAP(ex_table2, (ray_table_body<2, true>(T.a.table, T.items, vb)))
+CSGD_EXEC_WRAP(ex_table3, (ray_table_body<3, true>(T.a.table, T.items, vb)))
+CSGD_EXEC_WRAP(ex_rmax, (slot_rmax_body(T.a.table, T.items, vb)))
+CSGD_EXEC_WRAP(ex_gather2, (backproject_solver_body<2>(T.a.bp, T.items, T.steps, vb)))
+CSGD_EXEC_WRAP(ex_gather3, (backproject_solver_body<3>(T.a.bp, T.items, T.steps, vb)))
+CSGD_EXEC_WRAP(ex_scatter2, (scatter_body<2, 1>(T.a.sc, vb)))
+CSGD_EXEC_WRAP(ex_scatter3, (scatter_body<3, 1>(T.a.sc, vb)))
+CSGD_EXEC_WRAP(ex_convert, (scatter_convert_body(T.a.sc, vb)))
+CSGD_EXEC_WRAP(ex_fwd_table2, (forward_dual_body<2, 1, true, true>(T.a.fwd, vb)))
+CSGD_EXEC_WRAP(ex_fwd_table3, (forward_dual_body<3, 1, true, true>(T.a.fwd, vb)))
+CSGD_EXEC_WRAP(ex_fwd_inline2, (forward_dual_body<2, 1, false, true>(T.a.fwd, vb)))
+CSGD_EXEC_WRAP(ex_fwd_inline3, (forward_dual_body<3, 1, false, true>(T.a.fwd, vb)))
+CSGD_EXEC_WRAP(ex_epilogue, (epilogue_body(T.a.epi, vb)))
+CSGD_EXEC_WRAP(ex_apply, (apply_pending_body(T.a.misc.r, T.a.misc.d, T.a.misc.n, vb)))
+CSGD_EXEC_WRAP(ex_average, (average_body(T.a.misc.G, T.a.misc.x, T.a.misc.xh, T.a.misc.cnt, vb)))
+CSGD_EXEC_WRAP(ex_clear, (clear_counts_body(T.a.misc.cnt, (int)T.a.misc.n)))
+CSGD_EXEC_WRAP(ex_xout, (tile_to_rowmajor_body(T.a.misc.G, T.a.misc.xt, T.a.misc.out, vb)))
+#undef CSGD_EXEC_WRAP
+
+__device__ __forceinline__ void run_unit(const ExecTask& T, unsigned long long w) {
+    VBlock vb;
+    vb.gx = T.gx;
+    vb.gy = T.gy;
+    vb.gz = T.gz;
+    vb.x = (unsigned)(w % T.gx);
+    vb.y = (unsigned)((w / T.gx) % T.gy);
+    vb.z = (unsigned)(w / ((unsigned long long)T.gx * T.gy));
+    switch (T.kind) {
+        case kExTable2: ex_table2(T, vb); break;
+        case kExTable3: ex_table3(T, vb); break;
+        case kExRmax: ex_rmax(T, vb); break;
+        case kExGather2: ex_gather2(T, vb); break;
+        case kExGather3: ex_gather3(T, vb); break;
+        case kExScatter2: ex_scatter2(T, vb); break;
+        case kExScatter3: ex_scatter3(T, vb); break;
+        case kExConvert: ex_convert(T, vb); break;
+        case kExFwdTable2: ex_fwd_table2(T, vb); break;
+        case kExFwdTable3: ex_fwd_table3(T, vb); break;
+        case kExFwdInline2: ex_fwd_inline2(T, vb); break;
+        case kExFwdInline3: ex_fwd_inline3(T, vb); break;
+        case kExEpilogue: ex_epilogue(T, vb); break;
+        case kExApply: ex_apply(T, vb); break;
+        case kExAverage: ex_average(T, vb); break;
+        case kExClear: ex_clear(T, vb); break;
+        case kExXout: ex_xout(T, vb); break;
+        default: break;
+    }
+}
+
+constexpr int kExecThreads = 256;
+
+__global__ void __launch_bounds__(kExecThreads, 4) k_executor(const ExecArgs e) {
+    __shared__ int s_task;
+    __shared__ unsigned long long s_unit;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int task = -1;
+            unsigned long long u = 0;
+            if (!ld_relaxed_gpu(e.status)) {
+                u = atomicAdd(e.ticket, 1ull);
+                if (u < e.n_units) {
+                    int lo = 0, hi = e.n_tasks - 1;  // the task whose units hold ticket u
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (e.prefix[mid] <= u) lo = mid; else hi = mid - 1;
+                    }
+                    task = lo;
+                    const unsigned dep = e.tasks[task].dep;
+                    const unsigned* cnt = e.done + e.tasks[task].problem;
+                    if (ld_acquire_gpu(cnt) < dep) {
+                        const long long t0 = global_ns();
+                        unsigned sleep = 32;
+                        while (ld_acquire_gpu(cnt) < dep) {
+                            if (ld_relaxed_gpu(e.status)) { task = -1; break; }
+                            if (global_ns() - t0 > e.wait_ns) {
+                                atomicExch(e.status, 1);
+                                task = -1;
+                                break;
+                            }
+                            __nanosleep(sleep);
+                            sleep = sleep < 2048 ? 2 * sleep : sleep;
+                        }
+                    }
+                    __threadfence();
+                }
+            }
+            s_task = task;
+            s_unit = u;
+        }
+        __syncthreads();
+        const int task = s_task;
+        if (task < 0) return;
+        const ExecTask& T = e.tasks[task];
+        run_unit(T, s_unit - e.prefix[task]);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(e.done + T.problem, 1u);
+        }
+    }
+}
 
 }  // namespace
 
@@ -1777,6 +2044,274 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
     if (e == cudaSuccess) e = cudaGetLastError();
     if (ev) cudaEventRecord(ev[3], s);
     return e;
+}
+
+// ---------------------------------------------------------------------------
+// Batch executor plan (host side)
+// ---------------------------------------------------------------------------
+struct ExecPlan {
+    std::vector<std::vector<ExecTask>> lists;  // per problem, in solve order
+    ExecTask* d_tasks = nullptr;
+    unsigned long long* d_prefix = nullptr;
+    unsigned long long* d_ticket = nullptr;
+    unsigned* d_done = nullptr;
+    int* d_status = nullptr;
+    int n_tasks = 0;
+    unsigned long long n_units = 0;
+    int grid = 0;
+    long long wait_ns = 0;
+};
+
+static ExecTask exec_task(int kind, int problem, int64_t gx, int64_t gy, int64_t gz,
+                          const WorkItem* items, const StepDesc* steps) {
+    ExecTask t;
+    memset(&t, 0, sizeof(t));
+    t.kind = kind;
+    t.problem = problem;
+    t.gx = (uint32_t)std::max<int64_t>(1, gx);
+    t.gy = (uint32_t)std::max<int64_t>(1, gy);
+    t.gz = (uint32_t)std::max<int64_t>(1, gz);
+    t.units = t.gx * t.gy * t.gz;
+    t.items = items;
+    t.steps = steps;
+    return t;
+}
+
+ExecPlan* exec_plan_new(int n_problems) {
+    ExecPlan* P = new (std::nothrow) ExecPlan;
+    if (P) P->lists.resize(std::max(0, n_problems));
+    return P;
+}
+
+void exec_plan_free(ExecPlan* P) {
+    if (!P) return;
+    cudaFree(P->d_tasks);
+    cudaFree(P->d_prefix);
+    cudaFree(P->d_ticket);
+    cudaFree(P->d_done);
+    cudaFree(P->d_status);
+    delete P;
+}
+
+// The kernels of one batch of a solve (launch_batch) as executor tasks: the
+// same arguments and grids for 256-thread blocks, one lane per ray in the
+// forward and the scatter, four view groups per gather block, and the bricks'
+// batches run by the scatter.
+cudaError_t exec_plan_add_batch(ExecPlan* P, int problem, const DevGeom& G, const DevTile& tile,
+                                const WorkItem* items, const StepDesc* steps, const BatchLaunch& b,
+                                const SolverBuffers& sb, int sm_count) {
+    std::vector<ExecTask>& L = P->lists[problem];
+    const bool scatter = b.bp_groups == kBPScatter ||
+                         (b.bp_groups <= kBPBrick && b.bp_groups >= kBPBrickLast);
+    const bool d2 = G.dim == 2;
+    TableArgs ta;
+    ta.G = G;
+    ta.j = b.j;
+    ta.w_begin = b.w_begin;
+    ta.r = sb.r;
+    ta.table = sb.table;
+    ta.slot_stride = sb.table_stride;
+    ta.rmax = sb.rmax;
+    const int rows = item_rows(b.max_item_rays);
+    const int64_t tv = (int64_t)tile.n[0] * tile.n[1] * tile.n[2];
+    int n_gg = 0;
+    if (scatter) {
+        if (b.n_items > 0) {
+            ExecTask t = exec_task(kExRmax, problem, b.n_items, rows, 1, items, steps);
+            t.a.table = ta;
+            L.push_back(t);
+        }
+        ScatterArgs sa;
+        sa.G = G;
+        sa.items = items;
+        sa.steps = steps;
+        sa.first = b.first;
+        sa.lane_factor = 1.f;
+        sa.sb = sb;
+        const int64_t nb = (b.max_rays + kExecThreads - 1) / kExecThreads;
+        ExecTask t = exec_task(d2 ? kExScatter2 : kExScatter3, problem, nb, b.nslots, 1, items, steps);
+        t.a.sc = sa;
+        L.push_back(t);
+        n_gg = (int)std::max<int64_t>(1, (tv + kExecThreads - 1) / kExecThreads);
+        if (n_gg > sb.gg_stride) return cudaErrorInvalidValue;
+        t = exec_task(kExConvert, problem, n_gg, b.nslots, 1, items, steps);
+        t.a.sc = sa;
+        L.push_back(t);
+    } else {
+        if (b.n_items > 0) {
+            ExecTask t = exec_task(d2 ? kExTable2 : kExTable3, problem, b.n_items, rows, 1, items, steps);
+            t.a.table = ta;
+            L.push_back(t);
+        }
+        const BPPlan plan = plan_backprojection(G, tile, b.nslots, (b.n_items + b.nslots - 1) / b.nslots,
+                                                sm_count, kExecThreads / kBPVox);
+        if (plan.blocks > sb.gg_stride || plan.C * kBPVox != kExecThreads) return cudaErrorInvalidValue;
+        BPArgs a;
+        a.G = G;
+        a.first = b.first;
+        a.table = sb.table;
+        a.table_stride = sb.table_stride;
+        a.xt = sb.x;
+        a.gout = sb.g;
+        a.mode = 0;
+        a.accumulate = 0;
+        a.slot_stride = sb.g_stride;
+        a.gg_part = sb.gg_part;
+        a.gg_stride = sb.gg_stride;
+        a.nnz_slot = sb.nnz_slot;
+        ExecTask t = exec_task(d2 ? kExGather2 : kExGather3, problem, plan.blocks, 1, b.nslots, items,
+                               steps);
+        t.a.bp = a;
+        L.push_back(t);
+        n_gg = plan.blocks;
+    }
+    const int64_t nb = std::max<int64_t>(1, (b.max_rays + kExecThreads - 1) / kExecThreads);
+    if (nb > sb.max_fwd_blocks || nb > sb.qq_stride) return cudaErrorInvalidValue;
+    FwdSolverArgs f;
+    f.G = G;
+    f.items = items;
+    f.steps = steps;
+    f.first = b.first;
+    f.sync_epoch = b.sync_epoch;
+    f.n_gg = n_gg;
+    f.sb = sb;
+    const int fk = scatter ? (d2 ? kExFwdInline2 : kExFwdInline3) : (d2 ? kExFwdTable2 : kExFwdTable3);
+    ExecTask t = exec_task(fk, problem, nb, b.nslots, 1, items, steps);
+    t.a.fwd = f;
+    L.push_back(t);
+    EpiArgs ea;
+    ea.G = G;
+    ea.items = items;
+    ea.steps = steps;
+    ea.first = b.first;
+    ea.nslots = b.nslots;
+    ea.j = b.j;
+    ea.w_begin = b.w_begin;
+    ea.n_items = b.n_items;
+    ea.sync_epoch = b.sync_epoch;
+    ea.sb = sb;
+    const int64_t vox_blocks = std::max<int64_t>(1, (tv + (int64_t)kEpiThreads * rows - 1) /
+                                                       ((int64_t)kEpiThreads * rows));
+    t = exec_task(kExEpilogue, problem, b.n_items + vox_blocks, rows, 1, items, steps);
+    t.a.epi = ea;
+    L.push_back(t);
+    return cudaSuccess;
+}
+
+// An epoch close (launch_epoch_close) as tasks: pending residual change (epoch
+// sync), averages, clearing the candidate counts.
+void exec_plan_add_close(ExecPlan* P, int problem, const DevGeom& G, const SolverBuffers& sb,
+                         int64_t n_rays, int64_t max_tile_voxels, int sync_epoch) {
+    std::vector<ExecTask>& L = P->lists[problem];
+    ExecMisc m;
+    memset(&m, 0, sizeof(m));
+    m.G = G;
+    m.x = sb.x;
+    m.xh = sb.xh;
+    m.cnt = sb.cnt;
+    m.r = sb.r;
+    m.d = sb.d;
+    m.n = n_rays;
+    if (sync_epoch) {
+        ExecTask t = exec_task(kExApply, problem, std::min<int64_t>((n_rays + 255) / 256, 4096), 1, 1,
+                               nullptr, nullptr);
+        t.a.misc = m;
+        L.push_back(t);
+    }
+    ExecTask t = exec_task(kExAverage, problem, std::min<int64_t>((max_tile_voxels / 4 + 255) / 256, 1024),
+                           G.n_tiles, 1, nullptr, nullptr);
+    t.a.misc = m;
+    L.push_back(t);
+    m.n = G.n_tiles;
+    t = exec_task(kExClear, problem, 1, 1, 1, nullptr, nullptr);
+    t.a.misc = m;
+    L.push_back(t);
+}
+
+void exec_plan_add_xout(ExecPlan* P, int problem, const DevGeom& G, const float* xt, float* out,
+                        int64_t max_tile_voxels) {
+    ExecMisc m;
+    memset(&m, 0, sizeof(m));
+    m.G = G;
+    m.xt = xt;
+    m.out = out;
+    ExecTask t = exec_task(kExXout, problem, std::min<int64_t>((max_tile_voxels + 255) / 256, 1024),
+                           G.n_tiles, 1, nullptr, nullptr);
+    t.a.misc = m;
+    P->lists[problem].push_back(t);
+}
+
+// Interleave the problems' lists round-robin (task k of every problem, then
+// task k + 1), give each task the count of its problem's earlier units, upload.
+cudaError_t exec_plan_finalize(ExecPlan* P, int64_t wait_ns, int stall_last, int sm_count) {
+    std::vector<ExecTask> all;
+    std::vector<unsigned long long> prefix;
+    std::vector<uint64_t> done_units(P->lists.size(), 0);
+    size_t longest = 0;
+    for (const auto& l : P->lists) longest = std::max(longest, l.size());
+    unsigned long long units = 0;
+    for (size_t k = 0; k < longest; ++k)
+        for (size_t p = 0; p < P->lists.size(); ++p) {
+            if (k >= P->lists[p].size()) continue;
+            ExecTask t = P->lists[p][k];
+            if (done_units[p] + t.units >= ((uint64_t)1 << 32)) return cudaErrorInvalidValue;
+            t.dep = (uint32_t)done_units[p];
+            if (stall_last && p == 0 && k + 1 == P->lists[p].size()) t.dep += 1;  // never satisfied
+            done_units[p] += t.units;
+            prefix.push_back(units);
+            units += t.units;
+            all.push_back(t);
+        }
+    prefix.push_back(units);
+    if (all.empty()) return cudaErrorInvalidValue;
+    P->n_tasks = (int)all.size();
+    P->n_units = units;
+    P->wait_ns = wait_ns;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_executor, kExecThreads, 0);
+    if (e != cudaSuccess) return e;
+    P->grid = std::max(1, per_sm) * std::max(1, sm_count);
+    e = cudaMalloc(&P->d_tasks, sizeof(ExecTask) * all.size());
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_prefix, sizeof(unsigned long long) * prefix.size());
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_ticket, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_done, sizeof(unsigned) * std::max<size_t>(1, P->lists.size()));
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_status, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->d_tasks, all.data(), sizeof(ExecTask) * all.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->d_prefix, prefix.data(), sizeof(unsigned long long) * prefix.size(),
+                       cudaMemcpyHostToDevice);
+    return e;
+}
+
+// Capturable: counters cleared, then the persistent launch.
+cudaError_t exec_plan_launch(ExecPlan* P, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(P->d_ticket, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(P->d_done, 0, sizeof(unsigned) * std::max<size_t>(1, P->lists.size()), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->d_status, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    ExecArgs a;
+    a.tasks = P->d_tasks;
+    a.prefix = P->d_prefix;
+    a.n_tasks = P->n_tasks;
+    a.n_units = P->n_units;
+    a.ticket = P->d_ticket;
+    a.done = P->d_done;
+    a.status = P->d_status;
+    a.wait_ns = P->wait_ns;
+    k_executor<<<P->grid, kExecThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t exec_plan_status(ExecPlan* P, int* status) {
+    return cudaMemcpy(status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+}
+
+void exec_plan_info(const ExecPlan* P, int* n_tasks, int64_t* n_units, int* grid) {
+    *n_tasks = P->n_tasks;
+    *n_units = (int64_t)P->n_units;
+    *grid = P->grid;
 }
 
 cudaError_t launch_epoch_close(const DevGeom& G, const SolverBuffers& sb, int64_t n_rays,

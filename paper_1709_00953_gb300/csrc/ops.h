@@ -122,4 +122,26 @@ cudaError_t launch_tile_to_rowmajor(const DevGeom& G, const float* xt, float* ou
 cudaError_t launch_sq_residual(const float* y, const float* ax, int64_t n, double* out,
                                cudaStream_t s);
 
+// ---- batch executor: the kernels of many solves in one persistent launch ----
+struct ExecPlan;
+ExecPlan* exec_plan_new(int n_problems);
+void exec_plan_free(ExecPlan* p);
+// the kernels of one batch of problem `problem`'s solve (see launch_batch)
+cudaError_t exec_plan_add_batch(ExecPlan* p, int problem, const DevGeom& G, const DevTile& tile,
+                                const WorkItem* items, const StepDesc* steps, const BatchLaunch& b,
+                                const SolverBuffers& sb, int sm_count);
+// an epoch close (see launch_epoch_close) and the row-major copy of x
+void exec_plan_add_close(ExecPlan* p, int problem, const DevGeom& G, const SolverBuffers& sb,
+                         int64_t n_rays, int64_t max_tile_voxels, int sync_epoch);
+void exec_plan_add_xout(ExecPlan* p, int problem, const DevGeom& G, const float* xt, float* out,
+                        int64_t max_tile_voxels);
+// interleave and upload; wait_ns bounds every wait; stall_last makes the last
+// task of problem 0 wait for a unit that never completes (tests of the bound)
+cudaError_t exec_plan_finalize(ExecPlan* p, int64_t wait_ns, int stall_last, int sm_count);
+// counters cleared, then the persistent launch (capturable into a graph)
+cudaError_t exec_plan_launch(ExecPlan* p, cudaStream_t s);
+// 0, or 1 when a wait of the last launch ran out (synchronous)
+cudaError_t exec_plan_status(ExecPlan* p, int* status);
+void exec_plan_info(const ExecPlan* p, int* n_tasks, int64_t* n_units, int* grid);
+
 }  // namespace csgd

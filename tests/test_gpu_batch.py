@@ -1,7 +1,13 @@
-"""Batched solves (one CUDA-graph launch for many problems) against solo solves (GPU).
+"""Batched solves against solo solves and the oracle (GPU).
 
-The batched and the one-by-one paths run the same deterministic kernels on
-independent state, so every problem's reconstruction must be identical.
+Two batched forms: one persistent launch of the executor with its device work
+queue (``Batch.launch``), and a graph of the problems' solve graphs
+(``Batch.launch_graphs``).  The graph form runs the same deterministic kernels
+on independent state as the one-by-one solves, so it must equal them bit for
+bit; the executor runs the same kernel bodies with one lane per ray and
+256-thread blocks, so it must equal them to rounding, repeat itself bit for
+bit, and match the oracle.  A bounded wait that runs out must end the launch
+with CSGD_ERR_TIMEOUT and leave the context usable.
 """
 import numpy as np
 import pytest
@@ -52,7 +58,7 @@ def test_batch_equals_one_by_one(mods):
     csgd, batch = mods
     probs = _problems(batch, 6)
     b = batch.Batch(probs)
-    b.launch()
+    b.launch_graphs()
     torch.cuda.synchronize()
     xs = [p.x.clone() for p in probs]
     for p in probs:
@@ -61,6 +67,82 @@ def test_batch_equals_one_by_one(mods):
     for p, xb in zip(probs, xs):
         assert torch.equal(p.x, xb), p.cfg["name"]
         assert float(p.x.abs().max()) > 0
+    # the same graphs launched one after the other
+    for p in probs:
+        p.x.fill_(-1.0)
+    b.launch_sequential_graphs()
+    torch.cuda.synchronize()
+    for p, xb in zip(probs, xs):
+        assert torch.equal(p.x, xb), p.cfg["name"]
+
+
+def test_executor_equals_one_by_one_to_rounding(mods):
+    """The persistent launch: every problem's x within rounding of its own
+    host-launched solve with the executor's launch shapes (one lane per ray,
+    4 view groups), bit for bit from one launch to the next, status OK."""
+    csgd, batch = mods
+    probs = _problems(batch, 6)
+    for p in probs:
+        p.solver.set_launch(4, 1)
+    b = batch.Batch(probs)
+    info = b.executor.info()
+    assert info["tasks"] > 6 and info["units"] > info["tasks"] and info["blocks"] > 0
+    b.launch()
+    b.status()
+    xs = [p.x.clone() for p in probs]
+    for p in probs:
+        p.x.fill_(-1.0)
+    b.launch()
+    b.status()
+    for p, xe in zip(probs, xs):
+        assert torch.equal(p.x, xe), p.cfg["name"]
+    b.solve_one_by_one()
+    for p, xe in zip(probs, xs):
+        ref = p.x.double()
+        err = float(torch.sqrt(torch.mean((xe.double() - ref) ** 2)))
+        assert err <= 1e-5 * float(ref.abs().max()), (p.cfg["name"], err)
+
+
+def test_executor_3d_and_scatter(mods):
+    """Cone problems through the executor with the scatter backprojection (its
+    lines set up inline, max |r| per slot, fixed-point sums): within rounding
+    of the solvers' own solves."""
+    csgd, batch = mods
+    cfgs = [C.small_cone3d(n=20, views=12, nd=32, tiles=(2, 2, 2), group=3, steps=16),
+            C.small_cone3d(n=24, views=16, nd=40, tiles=(2, 2, 3), group=4, steps=20)]
+    probs = [batch.Problem(c, D.make_data(c)[0]) for c in cfgs]
+    for p in probs:
+        p.solver.set_launch(csgd.SCATTER, 1)
+    b = batch.Batch(probs)
+    b.launch()
+    b.status()
+    xs = [p.x.clone() for p in probs]
+    b.solve_one_by_one()
+    for p, xe in zip(probs, xs):
+        ref = p.x.double()
+        err = float(torch.sqrt(torch.mean((xe.double() - ref) ** 2)))
+        assert float(ref.abs().max()) > 0
+        assert err <= 1e-5 * float(ref.abs().max()), (p.cfg["name"], err)
+
+
+def test_executor_wait_runs_out(mods):
+    """The last task of the first problem waits for a block of work that never
+    completes (a test hook): its wait must run out after the limit (0.2 s of
+    GPU time), the launch end with CSGD_ERR_TIMEOUT, and the context stay
+    usable (a normal batch then runs)."""
+    csgd, batch = mods
+    probs = _problems(batch, 2)
+    stalled = csgd.Batch([p.solver for p in probs], [p.steps for p in probs],
+                         [p.x for p in probs], wait_limit_ns=200_000_000, stall_last_task=True)
+    stalled.launch()
+    with pytest.raises(csgd.CsgdError) as e:
+        stalled.status()
+    assert e.value.code == -4
+    del stalled
+    ok = csgd.Batch([p.solver for p in probs], [p.steps for p in probs], [p.x for p in probs])
+    ok.launch()
+    ok.status()
+    assert all(float(p.x.abs().max()) > 0 for p in probs)
 
 
 def test_graph_to_pinned_host(mods):
@@ -114,7 +196,7 @@ def test_launch_shapes_change_rounding_only(mods):
 def test_batch_matches_oracle(mods):
     """Batched solves against the FP64 oracle: three uneven problems of the
     batched workload's kind (curved fans, 8 view blocks x 4 x 4 tiles,
-    density-weighted choice), autotuned and solved together in one graph
+    density-weighted choice), autotuned and solved together in one persistent
     launch, each within RMSE 1e-4 of the oracle's literal run of its own
     schedule and step count."""
     from oracle.blocks import Partition as OPart
@@ -124,7 +206,7 @@ def test_batch_matches_oracle(mods):
     probs = _problems(batch, 3)
     b = batch.Batch(probs, autotune=True)
     b.launch()
-    torch.cuda.synchronize()
+    b.status()
     for p in probs:
         cfg = p.cfg
         og = OGeom(**cfg["geom"])
