@@ -1540,8 +1540,8 @@ struct ExecTask {
     int32_t problem;
     uint32_t gx, gy, gz;
     uint32_t units;
-    uint32_t dep;  // completed units of the problem that must precede this task
-    uint32_t pad;
+    uint32_t dep;    // completed units of the problem that must precede this task
+    uint32_t chunk;  // units per ticket (consecutive blocks run by one executor block)
     const WorkItem* items;
     const StepDesc* steps;
     union {
@@ -1554,11 +1554,14 @@ struct ExecTask {
     } a;
 };
 
+constexpr int kExecIndexStep = 256;  // tickets per entry of the coarse ticket -> task index
+
 struct ExecArgs {
     const ExecTask* tasks;
-    const unsigned long long* prefix;  // [n_tasks + 1]: units of the tasks before
+    const unsigned long long* prefix;  // [n_tasks + 1]: tickets of the tasks before
+    const int* index;  // [n_tickets / kExecIndexStep + 2]: task holding ticket k * kExecIndexStep
     int n_tasks;
-    unsigned long long n_units;
+    unsigned long long n_units;  // tickets
     unsigned long long* ticket;
     unsigned* done;  // [problem]: completed units
     int* status;     // 0, or 1 once a wait ran out
@@ -1650,7 +1653,9 @@ __global__ void __launch_bounds__(kExecThreads, 4) k_executor(const ExecArgs e) 
             if (!ld_relaxed_gpu(e.status)) {
                 u = atomicAdd(e.ticket, 1ull);
                 if (u < e.n_units) {
-                    int lo = 0, hi = e.n_tasks - 1;  // the task whose units hold ticket u
+                    // the task whose tickets hold u: between two entries of the coarse index
+                    const unsigned long long c = u / kExecIndexStep;
+                    int lo = e.index[c], hi = e.index[c + 1];
                     while (lo < hi) {
                         const int mid = (lo + hi + 1) >> 1;
                         if (e.prefix[mid] <= u) lo = mid; else hi = mid - 1;
@@ -1682,11 +1687,15 @@ __global__ void __launch_bounds__(kExecThreads, 4) k_executor(const ExecArgs e) 
         const int task = s_task;
         if (task < 0) return;
         const ExecTask& T = e.tasks[task];
-        run_unit(T, s_unit - e.prefix[task]);
-        __syncthreads();
+        const unsigned long long w0 = (s_unit - e.prefix[task]) * T.chunk;
+        const unsigned long long w1 = min(w0 + T.chunk, (unsigned long long)T.units);
+        for (unsigned long long w = w0; w < w1; ++w) {
+            run_unit(T, w);
+            __syncthreads();
+        }
         if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(e.done + T.problem, 1u);
+            atomicAdd(e.done + T.problem, (unsigned)(w1 - w0));
         }
     }
 }
@@ -2053,11 +2062,13 @@ struct ExecPlan {
     std::vector<std::vector<ExecTask>> lists;  // per problem, in solve order
     ExecTask* d_tasks = nullptr;
     unsigned long long* d_prefix = nullptr;
+    int* d_index = nullptr;
     unsigned long long* d_ticket = nullptr;
     unsigned* d_done = nullptr;
     int* d_status = nullptr;
     int n_tasks = 0;
-    unsigned long long n_units = 0;
+    unsigned long long n_units = 0;  // tickets
+    unsigned long long blocks = 0;   // thread blocks of all tasks
     int grid = 0;
     long long wait_ns = 0;
 };
@@ -2087,6 +2098,7 @@ void exec_plan_free(ExecPlan* P) {
     if (!P) return;
     cudaFree(P->d_tasks);
     cudaFree(P->d_prefix);
+    cudaFree(P->d_index);
     cudaFree(P->d_ticket);
     cudaFree(P->d_done);
     cudaFree(P->d_status);
@@ -2242,14 +2254,21 @@ void exec_plan_add_xout(ExecPlan* P, int problem, const DevGeom& G, const float*
 }
 
 // Interleave the problems' lists round-robin (task k of every problem, then
-// task k + 1), give each task the count of its problem's earlier units, upload.
+// task k + 1), give each task the count of its problem's earlier units and its
+// tickets (one per block of a small task; up to 16 consecutive blocks of a
+// large one, so that few blocks of the executor share the work of a task
+// with thousands of blocks), upload.
 cudaError_t exec_plan_finalize(ExecPlan* P, int64_t wait_ns, int stall_last, int sm_count) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_executor, kExecThreads, 0);
+    if (e != cudaSuccess) return e;
+    P->grid = std::max(1, per_sm) * std::max(1, sm_count);
     std::vector<ExecTask> all;
     std::vector<unsigned long long> prefix;
     std::vector<uint64_t> done_units(P->lists.size(), 0);
     size_t longest = 0;
     for (const auto& l : P->lists) longest = std::max(longest, l.size());
-    unsigned long long units = 0;
+    unsigned long long tickets = 0;
     for (size_t k = 0; k < longest; ++k)
         for (size_t p = 0; p < P->lists.size(); ++p) {
             if (k >= P->lists[p].size()) continue;
@@ -2257,21 +2276,27 @@ cudaError_t exec_plan_finalize(ExecPlan* P, int64_t wait_ns, int stall_last, int
             if (done_units[p] + t.units >= ((uint64_t)1 << 32)) return cudaErrorInvalidValue;
             t.dep = (uint32_t)done_units[p];
             if (stall_last && p == 0 && k + 1 == P->lists[p].size()) t.dep += 1;  // never satisfied
+            t.chunk = (uint32_t)std::min<int64_t>(16, std::max<int64_t>(1, (int64_t)t.units / P->grid));
             done_units[p] += t.units;
-            prefix.push_back(units);
-            units += t.units;
+            P->blocks += t.units;
+            prefix.push_back(tickets);
+            tickets += (t.units + t.chunk - 1) / t.chunk;
             all.push_back(t);
         }
-    prefix.push_back(units);
+    prefix.push_back(tickets);
     if (all.empty()) return cudaErrorInvalidValue;
+    std::vector<int> index(tickets / kExecIndexStep + 2, (int)all.size() - 1);
+    for (size_t c = 0, k = 0; c * kExecIndexStep < tickets; ++c) {
+        while (k + 1 < all.size() && prefix[k + 1] <= c * kExecIndexStep) ++k;
+        index[c] = (int)k;
+    }
     P->n_tasks = (int)all.size();
-    P->n_units = units;
+    P->n_units = tickets;
     P->wait_ns = wait_ns;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_executor, kExecThreads, 0);
-    if (e != cudaSuccess) return e;
-    P->grid = std::max(1, per_sm) * std::max(1, sm_count);
     e = cudaMalloc(&P->d_tasks, sizeof(ExecTask) * all.size());
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_index, sizeof(int) * index.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->d_index, index.data(), sizeof(int) * index.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&P->d_prefix, sizeof(unsigned long long) * prefix.size());
     if (e == cudaSuccess) e = cudaMalloc(&P->d_ticket, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&P->d_done, sizeof(unsigned) * std::max<size_t>(1, P->lists.size()));
@@ -2294,6 +2319,7 @@ cudaError_t exec_plan_launch(ExecPlan* P, cudaStream_t s) {
     ExecArgs a;
     a.tasks = P->d_tasks;
     a.prefix = P->d_prefix;
+    a.index = P->d_index;
     a.n_tasks = P->n_tasks;
     a.n_units = P->n_units;
     a.ticket = P->d_ticket;
@@ -2310,7 +2336,7 @@ cudaError_t exec_plan_status(ExecPlan* P, int* status) {
 
 void exec_plan_info(const ExecPlan* P, int* n_tasks, int64_t* n_units, int* grid) {
     *n_tasks = P->n_tasks;
-    *n_units = (int64_t)P->n_units;
+    *n_units = (int64_t)P->blocks;
     *grid = P->grid;
 }
 
