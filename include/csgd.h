@@ -333,9 +333,10 @@ int32_t csgd_graph_destroy(csgd_graph* graph);
  * kernels have completed, runs it and counts it as done.  Every such wait is
  * bounded by wait_limit_ns of GPU time (0 selects 2 s); a wait that runs out
  * stops the launch and csgd_batch_status returns CSGD_ERR_TIMEOUT.
- * The executor runs every solve with one lane per ray, 256-thread blocks and,
- * for the gather backprojection, 4 view groups per block (bricks run as the
- * scatter): results equal the solvers' own solves to rounding.  The solvers
+ * The executor runs every solve with its solver's lanes per ray (1 when the
+ * model chooses), 256-thread blocks and, for the gather backprojection, 4 view
+ * groups per block (bricks run as the scatter): results equal the solvers' own
+ * solves to rounding.  The solvers
  * must stay alive, on one device, all 2D or all 3D, and must not be used
  * otherwise while the batch may run (the batch keeps their planned schedules
  * on the device).

@@ -1275,7 +1275,7 @@ int32_t csgd_batch_create(csgd_solver* const* solvers, const int64_t* n_steps, f
                     (int64_t)(pl.items[w].u1 - pl.items[w].u0) * (pl.items[w].v1 - pl.items[w].v0));
             b.sync_epoch = S->prm.sync == CSGD_SYNC_EPOCH;
             b.bp_groups = S->bp_groups;
-            b.fwd_lanes = 1;
+            b.fwd_lanes = S->fwd_lanes;
             e = exec_plan_add_batch(B->plan, k, p.dg, p.tiles_h[op.j], S->d_items, S->d_steps, b, S->sb,
                                     S->P->sm_count);
             if (e != cudaSuccess) rc = cuda_fail(e, "batch task");

@@ -1506,22 +1506,28 @@ __global__ void k_sq_residual(const float* y, const float* ax, int64_t n, double
 //
 // The host lists, per problem, the kernels its solve would launch (ray table or
 // max |r| pass, backprojection, conversion, dual forward, epilogue, epoch
-// closes, x out) as tasks of `units` thread blocks each, and interleaves the
-// problems' lists round-robin.  A block of the executor takes the next unit
-// from a device ticket counter, waits until every unit of its problem's
-// earlier tasks has completed (a per-problem counter of completed units, read
-// with acquire semantics), runs the unit with the task's kernel body and its
-// virtual block index, and counts it as completed (release).  Tickets are
-// handed out in list order and a unit only waits for units of smaller tickets,
-// so the smallest outstanding unit can always run: no deadlock.  Every wait is
-// bounded (wait_ns of GPU time); a wait that runs out sets the status word, and
-// every block stops taking work once it is set.
+// closes, x out) as tasks of `units` thread blocks each.  On the device every
+// problem has a work word (its current task, next unit) and a count of the
+// current task's completed units.  An executor block takes a chunk of units
+// from the current task of a problem that has units left (atomic add on the
+// work word), starting from its home problem and moving on to the others; runs
+// them with the task's kernel body and virtual block indices; and adds them to
+// the completed count.  The block that completes a task's last unit publishes
+// the problem's next task (release: the task's writes are visible to the
+// blocks that then take its units).  So a block never waits for a dependency;
+// it only idles when no problem has units left, and that idling is bounded
+// (wait_ns of GPU time without work): then the status word is set and every
+// block stops.
 // ---------------------------------------------------------------------------
+// Task kinds; the forward and the scatter come in three lane counts (1, 2, 4
+// lanes per ray: kind + 0, 1, 2).
 enum ExecKind : int32_t {
-    kExTable2, kExTable3, kExRmax, kExGather2, kExGather3, kExScatter2, kExScatter3, kExConvert,
-    kExFwdTable2, kExFwdTable3, kExFwdInline2, kExFwdInline3, kExEpilogue, kExApply, kExAverage,
-    kExClear, kExXout
+    kExTable2, kExTable3, kExRmax, kExGather2, kExGather3, kExConvert, kExEpilogue, kExApply,
+    kExAverage, kExClear, kExXout,
+    kExScatter2 = 16, kExScatter3 = 19, kExFwdTable2 = 22, kExFwdTable3 = 25, kExFwdInline2 = 28,
+    kExFwdInline3 = 31
 };
+inline int lane_variant(int L) { return L == 4 ? 2 : (L == 2 ? 1 : 0); }
 
 struct ExecMisc {
     DevGeom G;
@@ -1540,8 +1546,8 @@ struct ExecTask {
     int32_t problem;
     uint32_t gx, gy, gz;
     uint32_t units;
-    uint32_t dep;    // completed units of the problem that must precede this task
-    uint32_t chunk;  // units per ticket (consecutive blocks run by one executor block)
+    uint32_t need;   // completed units that complete the task (= units)
+    uint32_t chunk;  // units one executor block takes at a time
     const WorkItem* items;
     const StepDesc* steps;
     union {
@@ -1554,23 +1560,21 @@ struct ExecTask {
     } a;
 };
 
-constexpr int kExecIndexStep = 256;  // tickets per entry of the coarse ticket -> task index
-
 struct ExecArgs {
-    const ExecTask* tasks;
-    const unsigned long long* prefix;  // [n_tasks + 1]: tickets of the tasks before
-    const int* index;  // [n_tickets / kExecIndexStep + 2]: task holding ticket k * kExecIndexStep
-    int n_tasks;
-    unsigned long long n_units;  // tickets
-    unsigned long long* ticket;
-    unsigned* done;  // [problem]: completed units
-    int* status;     // 0, or 1 once a wait ran out
+    const ExecTask* tasks;        // per problem, contiguous, in solve order
+    const int* first;             // [problem + 1]: first task of each problem
+    int n_problems;
+    int n_active;                 // problems with at least one task
+    unsigned long long* work;     // [problem]: current task << 32 | next unit
+    unsigned* done;               // [problem]: completed units of the current task
+    unsigned* finished;           // problems whose last task completed
+    int* status;                  // 0, or 1 once the idle bound ran out
     long long wait_ns;
 };
 
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
@@ -1597,13 +1601,18 @@ CSGD_EXEC_WRAP(ex_table3, (ray_table_body<3, true>(T.a.table, T.items, vb)))
 CSGD_EXEC_WRAP(ex_rmax, (slot_rmax_body(T.a.table, T.items, vb)))
 CSGD_EXEC_WRAP(ex_gather2, (backproject_solver_body<2>(T.a.bp, T.items, T.steps, vb)))
 CSGD_EXEC_WRAP(ex_gather3, (backproject_solver_body<3>(T.a.bp, T.items, T.steps, vb)))
-CSGD_EXEC_WRAP(ex_scatter2, (scatter_body<2, 1>(T.a.sc, vb)))
-CSGD_EXEC_WRAP(ex_scatter3, (scatter_body<3, 1>(T.a.sc, vb)))
 CSGD_EXEC_WRAP(ex_convert, (scatter_convert_body(T.a.sc, vb)))
-CSGD_EXEC_WRAP(ex_fwd_table2, (forward_dual_body<2, 1, true, true>(T.a.fwd, vb)))
-CSGD_EXEC_WRAP(ex_fwd_table3, (forward_dual_body<3, 1, true, true>(T.a.fwd, vb)))
-CSGD_EXEC_WRAP(ex_fwd_inline2, (forward_dual_body<2, 1, false, true>(T.a.fwd, vb)))
-CSGD_EXEC_WRAP(ex_fwd_inline3, (forward_dual_body<3, 1, false, true>(T.a.fwd, vb)))
+#define CSGD_EXEC_WRAP_L(name, L)                                                       \
+    CSGD_EXEC_WRAP(ex_scatter2_##name, (scatter_body<2, L>(T.a.sc, vb)))                \
+    CSGD_EXEC_WRAP(ex_scatter3_##name, (scatter_body<3, L>(T.a.sc, vb)))                \
+    CSGD_EXEC_WRAP(ex_fwd_table2_##name, (forward_dual_body<2, L, true, true>(T.a.fwd, vb)))  \
+    CSGD_EXEC_WRAP(ex_fwd_table3_##name, (forward_dual_body<3, L, true, true>(T.a.fwd, vb)))  \
+    CSGD_EXEC_WRAP(ex_fwd_inline2_##name, (forward_dual_body<2, L, false, true>(T.a.fwd, vb))) \
+    CSGD_EXEC_WRAP(ex_fwd_inline3_##name, (forward_dual_body<3, L, false, true>(T.a.fwd, vb)))
+CSGD_EXEC_WRAP_L(l1, 1)
+CSGD_EXEC_WRAP_L(l2, 2)
+CSGD_EXEC_WRAP_L(l4, 4)
+#undef CSGD_EXEC_WRAP_L
 CSGD_EXEC_WRAP(ex_epilogue, (epilogue_body(T.a.epi, vb)))
 CSGD_EXEC_WRAP(ex_apply, (apply_pending_body(T.a.misc.r, T.a.misc.d, T.a.misc.n, vb)))
 CSGD_EXEC_WRAP(ex_average, (average_body(T.a.misc.G, T.a.misc.x, T.a.misc.xh, T.a.misc.cnt, vb)))
@@ -1625,13 +1634,18 @@ __device__ __forceinline__ void run_unit(const ExecTask& T, unsigned long long w
         case kExRmax: ex_rmax(T, vb); break;
         case kExGather2: ex_gather2(T, vb); break;
         case kExGather3: ex_gather3(T, vb); break;
-        case kExScatter2: ex_scatter2(T, vb); break;
-        case kExScatter3: ex_scatter3(T, vb); break;
         case kExConvert: ex_convert(T, vb); break;
-        case kExFwdTable2: ex_fwd_table2(T, vb); break;
-        case kExFwdTable3: ex_fwd_table3(T, vb); break;
-        case kExFwdInline2: ex_fwd_inline2(T, vb); break;
-        case kExFwdInline3: ex_fwd_inline3(T, vb); break;
+#define CSGD_EXEC_CASES(base, fn)                      \
+        case base: fn##_l1(T, vb); break;              \
+        case base + 1: fn##_l2(T, vb); break;          \
+        case base + 2: fn##_l4(T, vb); break;
+        CSGD_EXEC_CASES(kExScatter2, ex_scatter2)
+        CSGD_EXEC_CASES(kExScatter3, ex_scatter3)
+        CSGD_EXEC_CASES(kExFwdTable2, ex_fwd_table2)
+        CSGD_EXEC_CASES(kExFwdTable3, ex_fwd_table3)
+        CSGD_EXEC_CASES(kExFwdInline2, ex_fwd_inline2)
+        CSGD_EXEC_CASES(kExFwdInline3, ex_fwd_inline3)
+#undef CSGD_EXEC_CASES
         case kExEpilogue: ex_epilogue(T, vb); break;
         case kExApply: ex_apply(T, vb); break;
         case kExAverage: ex_average(T, vb); break;
@@ -1644,58 +1658,98 @@ __device__ __forceinline__ void run_unit(const ExecTask& T, unsigned long long w
 constexpr int kExecThreads = 256;
 
 __global__ void __launch_bounds__(kExecThreads, 4) k_executor(const ExecArgs e) {
-    __shared__ int s_task;
-    __shared__ unsigned long long s_unit;
+    __shared__ int s_task, s_p;
+    __shared__ unsigned s_u, s_n;
+    // thread 0's state: the home problem (where the block last found work), the
+    // chunk it claims there, and the chunk run last (counted as done before
+    // the next claim)
+    int home = (int)(blockIdx.x % (unsigned)e.n_problems);
+    unsigned claim = 1;
+    int prev_task = -1, prev_p = 0;
+    unsigned prev_n = 0;
+    long long idle_since = -1;
     for (;;) {
         if (threadIdx.x == 0) {
-            int task = -1;
-            unsigned long long u = 0;
-            if (!ld_relaxed_gpu(e.status)) {
-                u = atomicAdd(e.ticket, 1ull);
-                if (u < e.n_units) {
-                    // the task whose tickets hold u: between two entries of the coarse index
-                    const unsigned long long c = u / kExecIndexStep;
-                    int lo = e.index[c], hi = e.index[c + 1];
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (e.prefix[mid] <= u) lo = mid; else hi = mid - 1;
+            if (prev_task >= 0) {
+                // the last chunk's writes, then its count; the block that
+                // completes a task publishes the problem's next one
+                __threadfence();
+                const ExecTask& T = e.tasks[prev_task];
+                if (atomicAdd(e.done + prev_p, prev_n) + prev_n == T.need) {
+                    e.done[prev_p] = 0;
+                    __threadfence();
+                    const int k = prev_task - e.first[prev_p];
+                    if (k + 1 == e.first[prev_p + 1] - e.first[prev_p]) atomicAdd(e.finished, 1u);
+                    atomicExch(e.work + prev_p, (unsigned long long)(k + 1) << 32);
+                }
+                prev_task = -1;
+            }
+            int task = -1, pf = 0;
+            unsigned u0 = 0, n = 0;
+            if (ld_relaxed_gpu(e.status)) {
+                task = -2;
+            } else {
+                for (int probe = 0; probe < e.n_problems && task < 0; ++probe) {
+                    const int p = (home + probe) % e.n_problems;
+                    const int ntask = e.first[p + 1] - e.first[p];
+                    if (probe > 0) {
+                        // another problem: look before claiming
+                        const unsigned long long w = ld_relaxed_gpu_u64(e.work + p);
+                        const int k = (int)(w >> 32);
+                        if (k >= ntask || (unsigned)w >= e.tasks[e.first[p] + k].units) continue;
+                        claim = e.tasks[e.first[p] + k].chunk;
                     }
-                    task = lo;
-                    const unsigned dep = e.tasks[task].dep;
-                    const unsigned* cnt = e.done + e.tasks[task].problem;
-                    if (ld_acquire_gpu(cnt) < dep) {
-                        const long long t0 = global_ns();
-                        unsigned sleep = 32;
-                        while (ld_acquire_gpu(cnt) < dep) {
-                            if (ld_relaxed_gpu(e.status)) { task = -1; break; }
-                            if (global_ns() - t0 > e.wait_ns) {
-                                atomicExch(e.status, 1);
-                                task = -1;
-                                break;
-                            }
-                            __nanosleep(sleep);
-                            sleep = sleep < 2048 ? 2 * sleep : sleep;
+                    // claim `claim` units; whatever task the problem is at by
+                    // then, they are units of that task (exactly `claim` of them)
+                    const unsigned long long got = atomicAdd(e.work + p, (unsigned long long)claim);
+                    const int k2 = (int)(got >> 32);
+                    if (k2 >= ntask) continue;
+                    const ExecTask& T = e.tasks[e.first[p] + k2];
+                    const unsigned u = (unsigned)got;
+                    if (u >= T.units) continue;
+                    task = e.first[p] + k2;
+                    pf = p;
+                    u0 = u;
+                    n = min(claim, T.units - u);
+                    home = p;  // stay with this problem while it has work
+                    claim = T.chunk;
+                }
+                if (task < 0) {
+                    if (ld_relaxed_gpu((const int*)e.finished) >= e.n_active) {
+                        task = -2;
+                    } else {
+                        const long long now = global_ns();
+                        if (idle_since < 0) idle_since = now;
+                        if (now - idle_since > e.wait_ns) {
+                            atomicExch(e.status, 1);
+                            task = -2;
+                        } else {
+                            __nanosleep(64);
                         }
                     }
-                    __threadfence();
+                } else {
+                    idle_since = -1;
+                    __threadfence();  // the task's inputs were published before its units
+                    prev_task = task;
+                    prev_p = pf;
+                    prev_n = n;
                 }
             }
             s_task = task;
-            s_unit = u;
+            s_p = pf;
+            s_u = u0;
+            s_n = n;
         }
         __syncthreads();
         const int task = s_task;
-        if (task < 0) return;
-        const ExecTask& T = e.tasks[task];
-        const unsigned long long w0 = (s_unit - e.prefix[task]) * T.chunk;
-        const unsigned long long w1 = min(w0 + T.chunk, (unsigned long long)T.units);
-        for (unsigned long long w = w0; w < w1; ++w) {
-            run_unit(T, w);
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(e.done + T.problem, (unsigned)(w1 - w0));
+        if (task == -2) return;
+        if (task >= 0) {
+            const ExecTask& T = e.tasks[task];
+            const unsigned u0 = s_u, n = s_n;
+            for (unsigned w = u0; w < u0 + n; ++w) {
+                run_unit(T, w);
+                __syncthreads();
+            }
         }
     }
 }
@@ -2061,14 +2115,14 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
 struct ExecPlan {
     std::vector<std::vector<ExecTask>> lists;  // per problem, in solve order
     ExecTask* d_tasks = nullptr;
-    unsigned long long* d_prefix = nullptr;
-    int* d_index = nullptr;
-    unsigned long long* d_ticket = nullptr;
+    int* d_first = nullptr;
+    unsigned long long* d_work = nullptr;
     unsigned* d_done = nullptr;
+    unsigned* d_finished = nullptr;
     int* d_status = nullptr;
     int n_tasks = 0;
-    unsigned long long n_units = 0;  // tickets
-    unsigned long long blocks = 0;   // thread blocks of all tasks
+    int n_active = 0;               // problems with at least one task
+    unsigned long long blocks = 0;  // thread blocks of all tasks
     int grid = 0;
     long long wait_ns = 0;
 };
@@ -2097,25 +2151,27 @@ ExecPlan* exec_plan_new(int n_problems) {
 void exec_plan_free(ExecPlan* P) {
     if (!P) return;
     cudaFree(P->d_tasks);
-    cudaFree(P->d_prefix);
-    cudaFree(P->d_index);
-    cudaFree(P->d_ticket);
+    cudaFree(P->d_first);
+    cudaFree(P->d_work);
     cudaFree(P->d_done);
+    cudaFree(P->d_finished);
     cudaFree(P->d_status);
     delete P;
 }
 
 // The kernels of one batch of a solve (launch_batch) as executor tasks: the
-// same arguments and grids for 256-thread blocks, one lane per ray in the
-// forward and the scatter, four view groups per gather block, and the bricks'
-// batches run by the scatter.
+// same arguments and grids for 256-thread blocks, the solver's lanes per ray
+// (b.fwd_lanes, 1 if unset) in the forward and the scatter, four view groups
+// per gather block, and the bricks' batches run by the scatter.
 cudaError_t exec_plan_add_batch(ExecPlan* P, int problem, const DevGeom& G, const DevTile& tile,
                                 const WorkItem* items, const StepDesc* steps, const BatchLaunch& b,
                                 const SolverBuffers& sb, int sm_count) {
-    std::vector<ExecTask>& L = P->lists[problem];
+    std::vector<ExecTask>& out = P->lists[problem];
     const bool scatter = b.bp_groups == kBPScatter ||
                          (b.bp_groups <= kBPBrick && b.bp_groups >= kBPBrickLast);
     const bool d2 = G.dim == 2;
+    const int L = b.fwd_lanes == 2 || b.fwd_lanes == 4 ? b.fwd_lanes : 1;
+    const int lv = lane_variant(L);
     TableArgs ta;
     ta.G = G;
     ta.j = b.j;
@@ -2131,29 +2187,30 @@ cudaError_t exec_plan_add_batch(ExecPlan* P, int problem, const DevGeom& G, cons
         if (b.n_items > 0) {
             ExecTask t = exec_task(kExRmax, problem, b.n_items, rows, 1, items, steps);
             t.a.table = ta;
-            L.push_back(t);
+            out.push_back(t);
         }
         ScatterArgs sa;
         sa.G = G;
         sa.items = items;
         sa.steps = steps;
         sa.first = b.first;
-        sa.lane_factor = 1.f;
+        sa.lane_factor = L > 1 ? 2.f : 1.f;
         sa.sb = sb;
-        const int64_t nb = (b.max_rays + kExecThreads - 1) / kExecThreads;
-        ExecTask t = exec_task(d2 ? kExScatter2 : kExScatter3, problem, nb, b.nslots, 1, items, steps);
+        const int64_t nb = (b.max_rays * L + kExecThreads - 1) / kExecThreads;
+        ExecTask t = exec_task((d2 ? kExScatter2 : kExScatter3) + lv, problem, nb, b.nslots, 1, items,
+                               steps);
         t.a.sc = sa;
-        L.push_back(t);
+        out.push_back(t);
         n_gg = (int)std::max<int64_t>(1, (tv + kExecThreads - 1) / kExecThreads);
         if (n_gg > sb.gg_stride) return cudaErrorInvalidValue;
         t = exec_task(kExConvert, problem, n_gg, b.nslots, 1, items, steps);
         t.a.sc = sa;
-        L.push_back(t);
+        out.push_back(t);
     } else {
         if (b.n_items > 0) {
             ExecTask t = exec_task(d2 ? kExTable2 : kExTable3, problem, b.n_items, rows, 1, items, steps);
             t.a.table = ta;
-            L.push_back(t);
+            out.push_back(t);
         }
         const BPPlan plan = plan_backprojection(G, tile, b.nslots, (b.n_items + b.nslots - 1) / b.nslots,
                                                 sm_count, kExecThreads / kBPVox);
@@ -2174,10 +2231,10 @@ cudaError_t exec_plan_add_batch(ExecPlan* P, int problem, const DevGeom& G, cons
         ExecTask t = exec_task(d2 ? kExGather2 : kExGather3, problem, plan.blocks, 1, b.nslots, items,
                                steps);
         t.a.bp = a;
-        L.push_back(t);
+        out.push_back(t);
         n_gg = plan.blocks;
     }
-    const int64_t nb = std::max<int64_t>(1, (b.max_rays + kExecThreads - 1) / kExecThreads);
+    const int64_t nb = std::max<int64_t>(1, (b.max_rays * L + kExecThreads - 1) / kExecThreads);
     if (nb > sb.max_fwd_blocks || nb > sb.qq_stride) return cudaErrorInvalidValue;
     FwdSolverArgs f;
     f.G = G;
@@ -2187,10 +2244,10 @@ cudaError_t exec_plan_add_batch(ExecPlan* P, int problem, const DevGeom& G, cons
     f.sync_epoch = b.sync_epoch;
     f.n_gg = n_gg;
     f.sb = sb;
-    const int fk = scatter ? (d2 ? kExFwdInline2 : kExFwdInline3) : (d2 ? kExFwdTable2 : kExFwdTable3);
+    const int fk = (scatter ? (d2 ? kExFwdInline2 : kExFwdInline3) : (d2 ? kExFwdTable2 : kExFwdTable3)) + lv;
     ExecTask t = exec_task(fk, problem, nb, b.nslots, 1, items, steps);
     t.a.fwd = f;
-    L.push_back(t);
+    out.push_back(t);
     EpiArgs ea;
     ea.G = G;
     ea.items = items;
@@ -2206,7 +2263,7 @@ cudaError_t exec_plan_add_batch(ExecPlan* P, int problem, const DevGeom& G, cons
                                                        ((int64_t)kEpiThreads * rows));
     t = exec_task(kExEpilogue, problem, b.n_items + vox_blocks, rows, 1, items, steps);
     t.a.epi = ea;
-    L.push_back(t);
+    out.push_back(t);
     return cudaSuccess;
 }
 
@@ -2253,77 +2310,62 @@ void exec_plan_add_xout(ExecPlan* P, int problem, const DevGeom& G, const float*
     P->lists[problem].push_back(t);
 }
 
-// Interleave the problems' lists round-robin (task k of every problem, then
-// task k + 1), give each task the count of its problem's earlier units and its
-// tickets (one per block of a small task; up to 16 consecutive blocks of a
-// large one, so that few blocks of the executor share the work of a task
-// with thousands of blocks), upload.
+// Upload the problems' task lists (contiguous, per problem); a task's chunk is
+// the units an executor block takes at a time: one for a task of fewer than
+// 128 blocks, up to 16 of a large one (about 64 claims per task).
 cudaError_t exec_plan_finalize(ExecPlan* P, int64_t wait_ns, int stall_last, int sm_count) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_executor, kExecThreads, 0);
     if (e != cudaSuccess) return e;
     P->grid = std::max(1, per_sm) * std::max(1, sm_count);
     std::vector<ExecTask> all;
-    std::vector<unsigned long long> prefix;
-    std::vector<uint64_t> done_units(P->lists.size(), 0);
-    size_t longest = 0;
-    for (const auto& l : P->lists) longest = std::max(longest, l.size());
-    unsigned long long tickets = 0;
-    for (size_t k = 0; k < longest; ++k)
-        for (size_t p = 0; p < P->lists.size(); ++p) {
-            if (k >= P->lists[p].size()) continue;
+    std::vector<int> first;
+    for (size_t p = 0; p < P->lists.size(); ++p) {
+        first.push_back((int)all.size());
+        P->n_active += P->lists[p].empty() ? 0 : 1;
+        for (size_t k = 0; k < P->lists[p].size(); ++k) {
             ExecTask t = P->lists[p][k];
-            if (done_units[p] + t.units >= ((uint64_t)1 << 32)) return cudaErrorInvalidValue;
-            t.dep = (uint32_t)done_units[p];
-            if (stall_last && p == 0 && k + 1 == P->lists[p].size()) t.dep += 1;  // never satisfied
-            t.chunk = (uint32_t)std::min<int64_t>(16, std::max<int64_t>(1, (int64_t)t.units / P->grid));
-            done_units[p] += t.units;
+            t.need = t.units;
+            if (stall_last && p == 0 && k + 1 == P->lists[p].size()) t.need += 1;  // never complete
+            t.chunk = (uint32_t)std::min<int64_t>(16, std::max<int64_t>(1, (int64_t)t.units / 64));
             P->blocks += t.units;
-            prefix.push_back(tickets);
-            tickets += (t.units + t.chunk - 1) / t.chunk;
             all.push_back(t);
         }
-    prefix.push_back(tickets);
-    if (all.empty()) return cudaErrorInvalidValue;
-    std::vector<int> index(tickets / kExecIndexStep + 2, (int)all.size() - 1);
-    for (size_t c = 0, k = 0; c * kExecIndexStep < tickets; ++c) {
-        while (k + 1 < all.size() && prefix[k + 1] <= c * kExecIndexStep) ++k;
-        index[c] = (int)k;
     }
+    first.push_back((int)all.size());
+    if (all.empty()) return cudaErrorInvalidValue;
     P->n_tasks = (int)all.size();
-    P->n_units = tickets;
     P->wait_ns = wait_ns;
+    const size_t np = std::max<size_t>(1, P->lists.size());
     e = cudaMalloc(&P->d_tasks, sizeof(ExecTask) * all.size());
-    if (e == cudaSuccess) e = cudaMalloc(&P->d_index, sizeof(int) * index.size());
-    if (e == cudaSuccess)
-        e = cudaMemcpy(P->d_index, index.data(), sizeof(int) * index.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&P->d_prefix, sizeof(unsigned long long) * prefix.size());
-    if (e == cudaSuccess) e = cudaMalloc(&P->d_ticket, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&P->d_done, sizeof(unsigned) * std::max<size_t>(1, P->lists.size()));
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_first, sizeof(int) * first.size());
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_work, sizeof(unsigned long long) * np);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_done, sizeof(unsigned) * np);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_finished, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&P->d_status, sizeof(int));
     if (e == cudaSuccess)
         e = cudaMemcpy(P->d_tasks, all.data(), sizeof(ExecTask) * all.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(P->d_prefix, prefix.data(), sizeof(unsigned long long) * prefix.size(),
-                       cudaMemcpyHostToDevice);
+        e = cudaMemcpy(P->d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice);
     return e;
 }
 
-// Capturable: counters cleared, then the persistent launch.
+// Capturable: work words, counts and status cleared, then the persistent launch.
 cudaError_t exec_plan_launch(ExecPlan* P, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(P->d_ticket, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(P->d_done, 0, sizeof(unsigned) * std::max<size_t>(1, P->lists.size()), s);
+    const size_t np = std::max<size_t>(1, P->lists.size());
+    cudaError_t e = cudaMemsetAsync(P->d_work, 0, sizeof(unsigned long long) * np, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->d_done, 0, sizeof(unsigned) * np, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->d_finished, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->d_status, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     ExecArgs a;
     a.tasks = P->d_tasks;
-    a.prefix = P->d_prefix;
-    a.index = P->d_index;
-    a.n_tasks = P->n_tasks;
-    a.n_units = P->n_units;
-    a.ticket = P->d_ticket;
+    a.first = P->d_first;
+    a.n_problems = (int)P->lists.size();
+    a.n_active = P->n_active;
+    a.work = P->d_work;
     a.done = P->d_done;
+    a.finished = P->d_finished;
     a.status = P->d_status;
     a.wait_ns = P->wait_ns;
     k_executor<<<P->grid, kExecThreads, 0, s>>>(a);

@@ -78,12 +78,13 @@ def test_batch_equals_one_by_one(mods):
 
 def test_executor_equals_one_by_one_to_rounding(mods):
     """The persistent launch: every problem's x within rounding of its own
-    host-launched solve with the executor's launch shapes (one lane per ray,
-    4 view groups), bit for bit from one launch to the next, status OK."""
+    host-launched solve with the executor's launch shapes (4 view groups, the
+    solver's lanes per ray: 1, 2 and 4 here), bit for bit from one launch to
+    the next, status OK."""
     csgd, batch = mods
     probs = _problems(batch, 6)
-    for p in probs:
-        p.solver.set_launch(4, 1)
+    for k, p in enumerate(probs):
+        p.solver.set_launch(4, (1, 2, 4)[k % 3])
     b = batch.Batch(probs)
     info = b.executor.info()
     assert info["tasks"] > 6 and info["units"] > info["tasks"] and info["blocks"] > 0
@@ -111,8 +112,8 @@ def test_executor_3d_and_scatter(mods):
     cfgs = [C.small_cone3d(n=20, views=12, nd=32, tiles=(2, 2, 2), group=3, steps=16),
             C.small_cone3d(n=24, views=16, nd=40, tiles=(2, 2, 3), group=4, steps=20)]
     probs = [batch.Problem(c, D.make_data(c)[0]) for c in cfgs]
-    for p in probs:
-        p.solver.set_launch(csgd.SCATTER, 1)
+    for p, lanes in zip(probs, (1, 2)):
+        p.solver.set_launch(csgd.SCATTER, lanes)
     b = batch.Batch(probs)
     b.launch()
     b.status()
