@@ -196,27 +196,32 @@ def cone3d_job(n: int, views: int, nd: int, tiles=(2, 2, 2), group: int = 30, ep
 
 
 def serving_jobs(n_jobs: int = 40, seed: int = 1709 + 4, small: bool = False) -> list:
-    """A seeded mix of reconstruction requests: 2D fan beams of 256^2 .. 1024^2 (or
-    64^2 .. 128^2 when small) and 3D cone beams of 64^3 .. 128^3 (24^3 .. 32^3 when
-    small), one in eight a 100^3-volume job with 360 views of 108^2 pixels (~4.2M
-    rays, the paper's "a million unknowns, four million measurements" scale)."""
+    """A seeded mix of reconstruction requests: 2D fan beams of 256^2 .. 2048^2
+    (64^2 .. 128^2 when small; 60 .. 720 views, 2 epochs) and 3D cone beams of
+    128^3 .. 512^3 (24^3 .. 32^3 when small; 60 .. 180 views of (1.5 n)^2
+    pixels, one epoch of groups of 30 views, 2^3 tiles up to 256^3 and 4^3
+    tiles above), sizes log-uniform; one in eight a 100^3-volume job with 360
+    views of 108^2 pixels (~4.2M rays, the paper's "a million unknowns, four
+    million measurements" scale)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for k in range(n_jobs):
         kind = rng.random()
-        if kind < 0.5:
-            lo, hi = (64, 128) if small else (256, 1024)
-            n = int(rng.integers(lo, hi + 1))
-            views = int(rng.integers(60, 360 if small else 720))
+        size = rng.random()
+        if kind < 0.45:
+            lo, hi = (64, 128) if small else (256, 2048)
+            n = int(round(lo * (hi / lo) ** size))
+            views = int(rng.integers(60, 360 if small else 721))
             cfg = batch_fan2d(1, seed=seed * 1000 + k, n_range=(n, n), views_range=(views, views),
                               epochs=2)[0]
             cfg["name"] = "serve_fan2d_%02d_%d_%d" % (k, n, views)
         elif kind < 0.875 or small:
-            lo, hi = (24, 32) if small else (64, 128)
-            n = int(rng.integers(lo, hi + 1))
-            views = int(rng.integers(24, 60 if small else 180))
+            lo, hi = (24, 32) if small else (128, 512)
+            n = int(round(lo * (hi / lo) ** size))
+            views = int(rng.integers(24, 60)) if small else int(rng.integers(60, 181))
             nd = int(1.5 * n)
-            cfg = cone3d_job(n, views, nd, group=min(10, views), seed=k,
+            tiles = (2, 2, 2) if n <= 256 else (4, 4, 4)
+            cfg = cone3d_job(n, views, nd, tiles=tiles, group=min(10 if small else 30, views), seed=k,
                              name="serve_cone3d_%02d_%d_%d" % (k, n, views))
         else:
             cfg = cone3d_job(100, 360, 108, group=30, seed=k, name="serve_cone3d_%02d_100_4M" % k)
