@@ -101,6 +101,8 @@ def parse():
     ap.add_argument("--jobs", type=int, default=40, help="serve: number of requests")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and served forms reported beside the headline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library's launch-shape models instead of csgd_solver_autotune")
@@ -529,6 +531,22 @@ def run_gpu(args, cfg, world, rank, local):
         line["e2e"] = e2e
     if cpu:
         line["cpu_baseline"] = cpu
+    if world == 1 and not args.no_extras:
+        # the batched (64 uneven fans) and served (Poisson mix) forms, in the same
+        # run: their own short timings, reported beside the headline
+        line["also"] = {}
+        for name, fn in (("batch_fan64", run_batch), ("serve", run_serve)):
+            sub = argparse.Namespace(**vars(args))
+            sub.steps, sub.warmup = (6, 1) if name == "batch_fan64" else (args.steps, 2)
+            try:
+                r = fn(sub, world, rank, local, emit=False)
+                keep = ("metric", "value", "unit", "ms_per_step", "config", "forms", "speedup_vs_one_by_one",
+                        "speedup_vs_sequential_graphs", "equal_rmse", "latency", "capacity",
+                        "one_at_a_time", "served_equals_one_at_a_time", "max_concurrency", "executor",
+                        "clocks")
+                line["also"][name] = {k: r[k] for k in keep if k in r}
+            except Exception as ex:  # reported, never fatal to the headline
+                line["also"][name] = {"error": repr(ex)[:300]}
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -538,7 +556,7 @@ def run_gpu(args, cfg, world, rank, local):
 # ---------------------------------------------------------------------------
 # batched workload: 64 uneven fan problems, one graph launch vs one by one
 # ---------------------------------------------------------------------------
-def run_batch(args, world, rank, local):
+def run_batch(args, world, rank, local, emit=True):
     # a single-GPU workload: under torchrun rank 0 runs it and the others exit
     if rank != 0:
         return 0
@@ -627,6 +645,8 @@ def run_batch(args, world, rank, local):
     }
     if ck:
         line["clocks"] = ck
+    if not emit:
+        return line
     print(json.dumps(line))
     return 0
 
@@ -634,7 +654,7 @@ def run_batch(args, world, rank, local):
 # ---------------------------------------------------------------------------
 # serving workload: Poisson arrivals of mixed fan / cone jobs, continuous batching
 # ---------------------------------------------------------------------------
-def run_serve(args, world, rank, local):
+def run_serve(args, world, rank, local, emit=True):
     # a single-GPU workload: under torchrun rank 0 runs it and the others exit
     if rank != 0:
         return 0
@@ -697,6 +717,8 @@ def run_serve(args, world, rank, local):
     }
     if ck:
         line["clocks"] = ck
+    if not emit:
+        return line
     print(json.dumps(line))
     return 0
 
