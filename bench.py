@@ -68,7 +68,18 @@ def algorithmic_bytes(kernel: str, rays: int, tile_voxels: int) -> int:
 # edit changes the hash and voids the entry ("traffic" is then null).
 # "backproject" is the ray table plus the gather, or the ray table, the scatter
 # and its conversion pass: the unit the bench times.
-NCU_COUNTERS: dict = {}
+NCU_COUNTERS: dict = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
+    #   smsp__issue_active.avg.pct_of_peak_sustained_active,gpu__time_duration.sum
+    #   --clock-control none -k regex:"k_slot_rmax|k_backproject_scatter|k_scatter_convert|
+    #   k_forward_dual|k_epilogue" -s 10 -c 10 python bench.py --no-cpu --no-e2e --no-extras
+    #   --steps 1 --warmup 1 --launch=-1,1  (GB300; mean of two batches of 12 slots)
+    ("cone3d_256_360x384x384_360x64_g30", "335295b1769710f1"): {
+        "backproject": {"traffic": 55565000, "issue_active_pct": 58.4,
+                        "parts": "max |r| pass 14.6 MB + scatter 27.3 MB + conversion 13.6 MB"},
+        "forward_dual": {"traffic": 28519000, "issue_active_pct": 67.7},
+    },
+}
 KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/csrc/device.cuh",
                   "paper_1709_00953_gb300/csrc/common.h")
 

@@ -147,48 +147,54 @@ __device__ __forceinline__ bool clip_sliver(const float q[3], const float inv[3]
     return t0 < t1;
 }
 
-// The exact line of bin (ku, kv) of view `view`, in FP64 from the unrounded
-// frame (the line the per (view, tile) FP32 constants round), in the
-// coordinates of tile t (voxel units, centred on the tile): p0 + s d.
-__device__ __forceinline__ void exact_line(const DevGeom& G, int view, int ku, int kv,
-                                           const DevTile& t, double p0[3], double d[3]) {
-    const DevView64& V = G.views64[view];
-    if (G.kind == PARALLEL_2D) {
-        const double s = ((double)ku - (double)G.cu) * G.pu_d;
+// The exact line of bin (ku, kv) of a view, in FP64 from the unrounded frame V
+// (the line the per (view, tile) FP32 constants round), in the coordinates of
+// the tile whose centre is T (voxel units): p0 + s d.  The functions below are
+// the cold path of the line set-up (rare lines only): they take scalars, are
+// not inlined, and keep their FP64 arithmetic out of the set-up of every line.
+__device__ __forceinline__ void exact_line(const DevView64& V, int kind, float cu, float cv,
+                                           double pu, double pv, int ku, int kv, const float T[3],
+                                           double p0[3], double d[3]) {
+    if (kind == PARALLEL_2D) {
+        const double s = ((double)ku - (double)cu) * pu;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            p0[a] = s * V.eu[a] - (double)t.T[a];
+            p0[a] = s * V.eu[a] - (double)T[a];
             d[a] = V.dc[a];
         }
-    } else if (G.kind == FAN_2D_CURVED) {
+    } else if (kind == FAN_2D_CURVED) {
         double sg, cg;
-        sincos(((double)ku - (double)G.cu) * G.pu_d, &sg, &cg);
+        sincos(((double)ku - (double)cu) * pu, &sg, &cg);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            p0[a] = V.S[a] - (double)t.T[a];
+            p0[a] = V.S[a] - (double)T[a];
             d[a] = cg * V.dc[a] + sg * V.eu[a];
         }
     } else {
-        const double u = ((double)ku - (double)G.cu) * G.pu_d;
-        const double w = ((double)kv - (double)G.cv) * G.pv_d;
+        const double u = ((double)ku - (double)cu) * pu;
+        const double w = ((double)kv - (double)cv) * pv;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            p0[a] = V.S[a] - (double)t.T[a];
+            p0[a] = V.S[a] - (double)T[a];
             d[a] = V.sdd * V.dc[a] + u * V.eu[a] + w * V.ev[a];
         }
     }
 }
 
-// Chord (voxel units) of that exact line through tile t; at most 0 when it
-// misses the tile.  Half-open faces as in the walk: a line parallel to an
-// axis meets the tile when lo <= q < hi.
-__device__ __forceinline__ double exact_chord(const DevGeom& G, int view, int ku, int kv,
-                                              const DevTile& t) {
+// Chord (voxel units) of that exact line through the tile of centre T and size
+// n; at most 0 when it misses the tile.  Half-open faces as in the walk: a line
+// parallel to an axis meets the tile when lo <= q < hi.
+__device__ __noinline__ double exact_chord_of(const DevView64* V, int kind, int dim, float cu,
+                                              float cv, double pu, double pv, int ku, int kv,
+                                              float T0, float T1, float T2, int n0, int n1,
+                                              int n2) {
+    const float T[3] = {T0, T1, T2};
+    const int n[3] = {n0, n1, n2};
     double p0[3], d[3];
-    exact_line(G, view, ku, kv, t, p0, d);
+    exact_line(*V, kind, cu, cv, pu, pv, ku, kv, T, p0, d);
     double t0 = -INFINITY, t1 = INFINITY, dn = 0.0;
-    for (int a = 0; a < G.dim; ++a) {
-        const double lo = -0.5 * (double)t.n[a], hi = 0.5 * (double)t.n[a];
+    for (int a = 0; a < dim; ++a) {
+        const double lo = -0.5 * (double)n[a], hi = 0.5 * (double)n[a];
         dn += d[a] * d[a];
         if (d[a] == 0.0) {
             if (!(p0[a] >= lo && p0[a] < hi)) return -1.0;
@@ -201,6 +207,12 @@ __device__ __forceinline__ double exact_chord(const DevGeom& G, int view, int ku
     return (t1 - t0) * sqrt(dn);
 }
 
+__device__ __forceinline__ double exact_chord(const DevGeom& G, int view, int ku, int kv,
+                                              const DevTile& t) {
+    return exact_chord_of(G.views64 + view, G.kind, G.dim, G.cu, G.cv, G.pu_d, G.pv_d, ku, kv, t.T[0],
+                          t.T[1], t.T[2], t.n[0], t.n[1], t.n[2]);
+}
+
 // Coordinate along axis ax of a line parallel to that axis's planes, placed on
 // the same side of its nearest voxel face as the exact (FP64) line: the FP32
 // set-up may put a line that lies exactly on a face (a view at a multiple of
@@ -208,15 +220,23 @@ __device__ __forceinline__ double exact_chord(const DevGeom& G, int view, int ku
 // and so in the wrong voxel column (or tile) over its whole length.  A line
 // exactly on a face goes to the voxel above it (half-open voxels), one ulp
 // above the face, so that (face - q) / d is never 0 / 0 either.
-__device__ __forceinline__ float parallel_coord(const DevGeom& G, int view, int ku, int kv,
-                                                const DevTile& t, int ax) {
+__device__ __noinline__ float parallel_coord_of(const DevView64* V, int kind, float cu, float cv,
+                                                double pu, double pv, int ku, int kv, float T0,
+                                                float T1, float T2, int n_ax, int ax) {
+    const float T[3] = {T0, T1, T2};
     double p0[3], d[3];
-    exact_line(G, view, ku, kv, t, p0, d);
+    exact_line(*V, kind, cu, cv, pu, pv, ku, kv, T, p0, d);
     const double e = p0[ax];
-    const double hn = 0.5 * (double)t.n[ax];
+    const double hn = 0.5 * (double)n_ax;
     const double f = rint(e + hn) - hn;  // nearest face (an exact float)
     const float ff = (float)f, qa = (float)e;
     return e >= f ? fmaxf(qa, nextafterf(ff, INFINITY)) : fminf(qa, nextafterf(ff, -INFINITY));
+}
+
+__device__ __forceinline__ float parallel_coord(const DevGeom& G, int view, int ku, int kv,
+                                                const DevTile& t, int ax) {
+    return parallel_coord_of(G.views64 + view, G.kind, G.cu, G.cv, G.pu_d, G.pv_d, ku, kv, t.T[0],
+                             t.T[1], t.T[2], t.n[ax], ax);
 }
 
 // Incremental Siddon walk of the line q + t d through the box over t in
