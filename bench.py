@@ -70,14 +70,17 @@ def algorithmic_bytes(kernel: str, rays: int, tile_voxels: int) -> int:
 # and its conversion pass: the unit the bench times.
 NCU_COUNTERS: dict = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
-    #   smsp__issue_active.avg.pct_of_peak_sustained_active,gpu__time_duration.sum
+    #   smsp__issue_active.avg.pct_of_peak_sustained_active,
+    #   sm__throughput.avg.pct_of_peak_sustained_elapsed,gpu__time_duration.sum
     #   --clock-control none -k regex:"k_slot_rmax|k_backproject_scatter|k_scatter_convert|
     #   k_forward_dual|k_epilogue" -s 10 -c 10 python bench.py --no-cpu --no-e2e --no-extras
-    #   --steps 1 --warmup 1 --launch=-1,1  (GB300; mean of two batches of 12 slots)
-    ("cone3d_256_360x384x384_360x64_g30", "335295b1769710f1"): {
-        "backproject": {"traffic": 55565000, "issue_active_pct": 58.4,
+    #   --steps 1 --warmup 3 --launch=-1,1  (GB300; mean of two batches of 12 slots);
+    # the L2 figures from ncu --set full on the same command (-s 4 -c 2)
+    ("cone3d_256_360x384x384_360x64_g30", "d2f263ea5bfb3940"): {
+        "backproject": {"traffic": 55565000, "issue_active_pct": 60.6,
+                        "lts_throughput_pct": 81.7, "l2_atomic_input_active_pct": 58.7,
                         "parts": "max |r| pass 14.6 MB + scatter 27.3 MB + conversion 13.6 MB"},
-        "forward_dual": {"traffic": 28519000, "issue_active_pct": 67.7},
+        "forward_dual": {"traffic": 28100000, "issue_active_pct": 69.0},
     },
 }
 KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/csrc/device.cuh",
@@ -476,15 +479,19 @@ def run_gpu(args, cfg, world, rank, local):
         roof["dram_gbs"] = traffic * n_launch / dom_s / 1e9
         roof["dram_frac"] = roof["dram_gbs"] / hbm
         roof["traffic_over_algorithmic"] = traffic / alg_launch
-    if counters.get("issue_active_pct") is not None:
-        roof["issue_active_pct"] = counters["issue_active_pct"]
+    for key in ("issue_active_pct", "lts_throughput_pct", "l2_atomic_input_active_pct"):
+        if counters.get(key) is not None:
+            roof[key] = counters[key]
     # the whole step against the same roof: SURVEY-style bytes 4 (2 R + 3 |J|) per step
     step_bytes = 4 * (2 * rep["rays"] + 3 * rep["tile_voxels"]) * args.steps
     roof["step_bytes_gbs"] = step_bytes / (ms / 1e3) / 1e9
-    # per batch: ray table + backprojection, dual forward, epilogue; per epoch close:
+    # per batch: the backprojection (ray table + gather; max |r| pass + scatter +
+    # conversion; or one brick kernel), dual forward, epilogue; per epoch close:
     # averaging (+ pending-residual apply under epoch sync)
     close_kernels = 2 if cfg["solver"].get("sync", 0) == 1 else 1
-    launches = int(2 * prof["backproject"]["launches"] + prof["forward_dual"]["launches"]
+    bp_form = shapes[0] if shapes else 0
+    bp_kernels = 3 if bp_form == csgd.SCATTER else (1 if bp_form in csgd.BRICKS else 2)
+    launches = int(bp_kernels * prof["backproject"]["launches"] + prof["forward_dual"]["launches"]
                    + prof["epilogue"]["launches"] + close_kernels * prof["epoch_close"]["launches"])
     kernels = {k: {"launches": int(v["launches"]), "ms": v["ms"],
                    "share": (v["ms"] / total_ms if total_ms else 0.0)} for k, v in kern.items()}
