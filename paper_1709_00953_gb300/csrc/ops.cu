@@ -1009,6 +1009,13 @@ __global__ void __maxnreg__(64) k_backproject_scatter(const ScatterArgs a) {
 }
 
 constexpr int kConvThreads = 256;
+constexpr int kConvPerThread = 4;  // voxels per thread, kConvThreads apart
+
+// CTAs of the conversion pass for a tile of tv voxels (one g^T g partial each)
+static inline int conv_blocks(int64_t tv) {
+    const int64_t per = (int64_t)kConvThreads * kConvPerThread;
+    return (int)std::max<int64_t>(1, (tv + per - 1) / per);
+}
 
 // g_J = h 2^-S acc (one rounding from the exact fixed-point sum), the pairs
 // (x_J, g_J) for the dual forward, a g^T g partial per CTA (FP32 as in the
@@ -1027,12 +1034,31 @@ __device__ __forceinline__ void scatter_convert_body(const ScatterArgs& a, const
     float2* gout = reinterpret_cast<float2*>(a.sb.g) + (int64_t)slot * a.sb.g_stride;
     const float* xt = a.sb.x + t.voff;
     float gg = 0.f;
-    for (int v = vb.x * blockDim.x + threadIdx.x; v < nvox; v += vb.gx * blockDim.x) {
-        const int s = __ldcg(acc + v);  // summed by L2 atomics
-        acc[v] = 0;
-        const float g = (float)s * isc * G.h;
-        gout[v] = make_float2(xt[v], g);
-        gg = fmaf(g, g, gg);
+    // kConvPerThread voxels a thread, their loads issued together
+    const int span = blockDim.x * kConvPerThread;
+    for (int v0 = vb.x * span + threadIdx.x; v0 < nvox; v0 += vb.gx * span) {
+        int s[kConvPerThread];
+        float xv[kConvPerThread];
+#pragma unroll
+        for (int k = 0; k < kConvPerThread; ++k) {
+            const int v = v0 + k * blockDim.x;
+            s[k] = 0;
+            xv[k] = 0.f;
+            if (v < nvox) {
+                s[k] = __ldcg(acc + v);  // summed by L2 atomics
+                xv[k] = xt[v];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kConvPerThread; ++k) {
+            const int v = v0 + k * blockDim.x;
+            if (v < nvox) {
+                acc[v] = 0;
+                const float g = (float)s[k] * isc * G.h;
+                gout[v] = make_float2(xv[k], g);
+                gg = fmaf(g, g, gg);
+            }
+        }
     }
     __shared__ float s_gg[kMaxBlock / 32];
     const float wg = warp_sum_f(gg);
@@ -2048,7 +2074,7 @@ cudaError_t launch_batch(const DevGeom& G, const DevTile& tile, const WorkItem* 
         }
         if (e != cudaSuccess) return e;
         const int64_t tv = (int64_t)tile.n[0] * tile.n[1] * tile.n[2];
-        n_gg = (int)std::max<int64_t>(1, (tv + kConvThreads - 1) / kConvThreads);
+        n_gg = conv_blocks(tv);
         if (n_gg > sb.gg_stride) return cudaErrorInvalidValue;
         e = launch_pdl(k_scatter_convert, dim3((unsigned)n_gg, b.nslots), dim3(kConvThreads), s, sa);
         if (e != cudaSuccess) return e;
@@ -2201,7 +2227,8 @@ cudaError_t exec_plan_add_batch(ExecPlan* P, int problem, const DevGeom& G, cons
                                steps);
         t.a.sc = sa;
         out.push_back(t);
-        n_gg = (int)std::max<int64_t>(1, (tv + kExecThreads - 1) / kExecThreads);
+        static_assert(kExecThreads == kConvThreads, "the conversion runs in executor blocks");
+        n_gg = conv_blocks(tv);
         if (n_gg > sb.gg_stride) return cudaErrorInvalidValue;
         t = exec_task(kExConvert, problem, n_gg, b.nslots, 1, items, steps);
         t.a.sc = sa;
