@@ -46,18 +46,26 @@ DEFAULT_STEPS = {"fan2d_512": 250, "parallel2d_64": 250, "cone3d_256": 16, "batc
 DEFAULT_WORKLOAD = "cone3d_256"
 
 
-def algorithmic_bytes(kernel: str, rays: int, tile_voxels: int) -> int:
-    """Bytes a kernel unit must move by the method's own definition, for steps
-    covering `rays` rays of their row blocks (in tile J's shadow) and
-    `tile_voxels` voxels of their tiles (FP32): the backprojection reads r and
-    writes g; the dual forward reads x_J and g_J and writes p and q; the
-    epilogue reads p, q, z and r, writes z and r, and reads g and updates x^."""
+def algorithmic_bytes(kernel: str, rays: int, tile_voxels: int, batch_voxels: int | None = None,
+                      volume_voxels: int = 0, epoch_rays: int = 0) -> int:
+    """Bytes a kernel unit must move by the method's own definition (FP32), for
+    steps covering `rays` rays of their row blocks (in tile J's shadow) and
+    `tile_voxels` voxels of their tiles: the backprojection reads r and writes
+    g; the dual forward reads x_J and g_J and writes p and q; the epilogue
+    reads p, q, z and r and writes z and r per ray, reads g_J per step and, once
+    per batch of steps on one tile (`batch_voxels` = the batches' tile voxels,
+    default one batch per step), reads x_J and updates x^_J; the epoch close
+    reads x^ and writes x and x^ over `volume_voxels` (and, under epoch sync,
+    reads the pending change and r and writes r over `epoch_rays`)."""
     if kernel == "backproject":
         return 4 * (rays + tile_voxels)
     if kernel == "forward_dual":
         return 4 * (2 * rays + 2 * tile_voxels)
     if kernel == "epilogue":
-        return 4 * (6 * rays + 3 * tile_voxels)
+        bv = tile_voxels if batch_voxels is None else batch_voxels
+        return 4 * (6 * rays + tile_voxels + 3 * bv)
+    if kernel == "epoch_close":
+        return 4 * (3 * volume_voxels + 3 * epoch_rays)
     return 0
 
 
@@ -482,6 +490,25 @@ def run_gpu(args, cfg, world, rank, local):
     for key in ("issue_active_pct", "lts_throughput_pct", "l2_atomic_input_active_pct"):
         if counters.get(key) is not None:
             roof[key] = counters[key]
+    # the HBM-bound kernels (the z and r update with the x^ accumulation, and the
+    # epoch close) against the same roof, on their algorithmic bytes
+    hbm_k = {}
+    n_epi = int(prof["epilogue"]["launches"])
+    if n_epi:
+        batch_vox = rep["tile_voxels"] * (n_epi / args.steps) / steps
+        b = algorithmic_bytes("epilogue", rep["rays"], rep["tile_voxels"], batch_vox) * args.steps / n_epi
+        t = prof["epilogue"]["ms"] / n_epi / 1e3
+        hbm_k["epilogue"] = {"algorithmic_bytes_per_launch": b, "ms_per_launch": t * 1e3,
+                             "achieved_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
+    n_close = int(prof["epoch_close"]["launches"])
+    if n_close:
+        sync_epoch = cfg["solver"].get("sync", 0) == 1
+        b = algorithmic_bytes("epoch_close", 0, 0, volume_voxels=p.n_voxels,
+                              epoch_rays=p.n_rays if sync_epoch else 0)
+        t = prof["epoch_close"]["ms"] / n_close / 1e3
+        hbm_k["epoch_close"] = {"algorithmic_bytes_per_launch": b, "ms_per_launch": t * 1e3,
+                                "achieved_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
+    roof["hbm_kernels"] = hbm_k
     # the whole step against the same roof: SURVEY-style bytes 4 (2 R + 3 |J|) per step
     step_bytes = 4 * (2 * rep["rays"] + 3 * rep["tile_voxels"]) * args.steps
     roof["step_bytes_gbs"] = step_bytes / (ms / 1e3) / 1e9

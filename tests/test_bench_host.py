@@ -41,12 +41,19 @@ def test_kernel_hash_ignores_comments_but_not_code(tmp_path):
 
 def test_algorithmic_bytes_per_kernel():
     """4 bytes per FP32 value the method must move: r in and g out for the
-    backprojection; x_J, g_J in and p, q out for the dual forward."""
+    backprojection; x_J, g_J in and p, q out for the dual forward; p, q, z, r in
+    and z, r out per ray, g_J per step and x_J, x^_J in and x^_J out per batch
+    for the epilogue; x^ in, x and x^ out per voxel for the epoch close (and
+    d, r in and r out per ray under epoch sync)."""
     import bench
     assert bench.algorithmic_bytes("backproject", 1000, 64) == 4 * (1000 + 64)
     assert bench.algorithmic_bytes("forward_dual", 1000, 64) == 4 * (2000 + 128)
-    assert bench.algorithmic_bytes("epilogue", 10, 4) == 4 * (60 + 12)
+    assert bench.algorithmic_bytes("epilogue", 10, 4) == 4 * (60 + 4 + 12)
+    # 12 steps on one 64-voxel tile in one batch
+    assert bench.algorithmic_bytes("epilogue", 100, 12 * 64, 64) == 4 * (600 + 768 + 192)
     assert bench.algorithmic_bytes("epoch_close", 10, 4) == 0
+    assert bench.algorithmic_bytes("epoch_close", 0, 0, volume_voxels=1000) == 12000
+    assert bench.algorithmic_bytes("epoch_close", 0, 0, volume_voxels=1000, epoch_rays=50) == 12600
 
 
 def test_oracle_steps_split_groups_into_row_blocks():
