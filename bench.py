@@ -83,12 +83,13 @@ NCU_COUNTERS: dict = {
     #   --clock-control none -k regex:"k_slot_rmax|k_backproject_scatter|k_scatter_convert|
     #   k_forward_dual|k_epilogue" -s 10 -c 10 python bench.py --no-cpu --no-e2e --no-extras
     #   --steps 1 --warmup 3 --launch=-1,1  (GB300; mean of two batches of 12 slots);
-    # the L2 figures from ncu --set full on the same command (-s 6 -c 3)
-    ("cone3d_256_360x384x384_360x64_g30", "739cc68169fbf20e"): {
-        "backproject": {"traffic": 55566000, "issue_active_pct": 60.9,
+    # the L2 figures from ncu --set full on the same command (-s 6 -c 3), taken
+    # with the same scatter code (the sources differed in the averaging kernel)
+    ("cone3d_256_360x384x384_360x64_g30", "4ee6fd6b5ebe15c6"): {
+        "backproject": {"traffic": 55567000, "issue_active_pct": 60.6,
                         "lts_throughput_pct": 81.2, "l2_atomic_input_active_pct": 58.3,
                         "parts": "max |r| pass 14.6 MB + scatter 27.3 MB + conversion 13.6 MB"},
-        "forward_dual": {"traffic": 28046000, "issue_active_pct": 69.1},
+        "forward_dual": {"traffic": 28037000, "issue_active_pct": 69.0},
     },
 }
 KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/csrc/device.cuh",

@@ -1465,10 +1465,25 @@ __device__ __forceinline__ void average_body(const DevGeom& G, float* x, float* 
     float4* x4 = reinterpret_cast<float4*>(x + b0);
     float4* h4 = reinterpret_cast<float4*>(xh + b0);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int64_t k = tid; k < (b1 - b0) / 4; k += nth) {
-        const float4 h = h4[k];
-        if (c > 0) x4[k] = make_float4(h.x / (float)c, h.y / (float)c, h.z / (float)c, h.w / (float)c);
-        h4[k] = z4;
+    // four 16-byte groups a thread, nth apart, their loads issued together
+    const int64_t n4 = (b1 - b0) / 4;
+    for (int64_t k0 = tid; k0 < n4; k0 += nth * 4) {
+        float4 h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t k = k0 + u * nth;
+            h[u] = k < n4 ? h4[k] : z4;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t k = k0 + u * nth;
+            if (k < n4) {
+                if (c > 0)
+                    x4[k] = make_float4(h[u].x / (float)c, h[u].y / (float)c, h[u].z / (float)c,
+                                        h[u].w / (float)c);
+                h4[k] = z4;
+            }
+        }
     }
 }
 
@@ -2314,7 +2329,7 @@ void exec_plan_add_close(ExecPlan* P, int problem, const DevGeom& G, const Solve
         t.a.misc = m;
         L.push_back(t);
     }
-    ExecTask t = exec_task(kExAverage, problem, std::min<int64_t>((max_tile_voxels / 4 + 255) / 256, 1024),
+    ExecTask t = exec_task(kExAverage, problem, std::min<int64_t>((max_tile_voxels / 4 + 1023) / 1024, 1024),
                            G.n_tiles, 1, nullptr, nullptr);
     t.a.misc = m;
     L.push_back(t);
@@ -2417,7 +2432,7 @@ cudaError_t launch_epoch_close(const DevGeom& G, const SolverBuffers& sb, int64_
                                    s, sb.r, sb.d, n_rays);
         if (e != cudaSuccess) return e;
     }
-    int64_t nb = std::min<int64_t>((max_tile_voxels / 4 + 255) / 256, 1024);
+    int64_t nb = std::min<int64_t>((max_tile_voxels / 4 + 1023) / 1024, 1024);
     cudaError_t e = launch_pdl(k_average, dim3((unsigned)std::max<int64_t>(nb, 1), G.n_tiles), dim3(256),
                                s, G, sb.x, sb.xh, (const int32_t*)sb.cnt);
     if (e == cudaSuccess) e = cudaGetLastError();
