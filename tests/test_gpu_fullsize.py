@@ -198,6 +198,27 @@ def test_cone256_backproject_one_view(csgd, cone):
     assert np.abs(ref[vox]).max() > 0
 
 
+def test_cone256_backproject_one_view_nonnegative(csgd, cone):
+    """The same view and tile with a residual of one sign: no voxel sum
+    cancels, and the plain per-voxel bound holds but for voxels that lines
+    merely graze, whose few terms (1 - 4 lines of one view per voxel) carry
+    FP32 line placement (about 1e-5 voxel) over a short chord: at most 3% of
+    the tile and 100 times the bound (measured 2.1%, 74x)."""
+    cfg, p, op = cone
+    rng = np.random.default_rng(8)
+    r = (np.abs(rng.standard_normal(p.n_rays)) + 0.1).astype(np.float32)
+    view, j = 33, 26
+    gv = torch.zeros(p.n_voxels, dtype=torch.float32, device="cuda")
+    csgd.backproject_block(p, [view], j, torch.tensor(r, device="cuda"), gv)
+    rows = op.rows_of([view])
+    ref = OB.backproject_block(op, [view], j, r[rows].astype(np.float64))
+    vox = op.tile_voxels(j)
+    got = gv.cpu().numpy().astype(np.float64)[vox]
+    assert np.all(np.abs(got - ref[vox]) <= REL * ref[vox] + TAU_BP * np.abs(r).max())
+    st = record("cone3d_256", "backproject_block_nonneg", got, ref[vox], group=[view], j=j)
+    assert st["frac_over"] <= 0.03 and st["max_ratio"] <= 100.0, st
+
+
 def test_cone256_scheduled_group_steps(csgd, cone):
     """The first three group steps of the cone3d_256 solve as scheduled (Alg. 4:
     density-weighted draws of single-view row blocks, 30 per group, all on the

@@ -183,6 +183,39 @@ def test_backproject_block_parity(csgd, name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
+def test_backproject_nonnegative_residual_plain_bound(csgd, name):
+    """g_J = (A_I^J)^T r for a residual of one sign (as r = y at the first step):
+    no voxel sum cancels, so the plain bound 1e-5 max(|ref|, 1e-3 max|ref|)
+    applies per voxel as it does per ray in the forward.  Only voxels that
+    lines merely graze may exceed it: FP32 places a line to about 1e-5 voxel,
+    so a short chord carries an absolute error of about 1e-5 |r|, against a
+    floor of 1e-8 max|ref|.  In 2D a voxel sums many lines and the guard is
+    the forward's (at most 1% of the voxels, 25 times the bound; measured
+    0.6%, 6x); in 3D a voxel sums 1 - 4 lines of a view, a single grazing
+    chord is not averaged out, and the guard is 3% and 100 times (measured
+    0.6%, 37x)."""
+    cfg = CASES[name]
+    p, op = _pair(csgd, cfg)
+    g = op.geom
+    rng = np.random.default_rng(6)
+    r = (np.abs(rng.standard_normal(g.n_rays)) + 0.1).astype(np.float32)
+    rt = torch.tensor(r, device="cuda")
+    for grp, j in _groups(op):
+        gv = torch.zeros(g.grid.size, dtype=torch.float32, device="cuda")
+        csgd.backproject_block(p, grp, j, rt, gv)
+        rows = op.rows_of(grp)
+        ref = OB.backproject_block(op, grp, j, r[rows].astype(np.float64))
+        vox = op.tile_voxels(j)
+        got = gv.cpu().numpy().astype(np.float64)[vox]
+        tol = REL * ref[vox] + TAU_BP * g.h * np.abs(r).max()
+        assert np.all(np.abs(got - ref[vox]) <= tol)
+        st = record(name, "backproject_block_nonneg", got, ref[vox], group=list(map(int, grp)),
+                    j=int(j))
+        lim = (0.01, 25.0) if len(cfg["geom"]["n"]) == 2 else (0.03, 100.0)
+        assert st["frac_over"] <= lim[0] and st["max_ratio"] <= lim[1], st
+
+
+@pytest.mark.parametrize("name", list(CASES))
 def test_adjoint_identity_on_gpu(csgd, name):
     """<A_I^J x, r> = <x, (A_I^J)^T r>: the two kernels use identical lengths."""
     cfg = CASES[name]
