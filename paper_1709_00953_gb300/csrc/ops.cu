@@ -434,9 +434,18 @@ __device__ __forceinline__ void slot_rmax_body(const TableArgs& a, const WorkIte
     float rm = 0.f;
     for (int k = vb.y * blockDim.x + threadIdx.x; k < nr; k += vb.gy * blockDim.x)
         rm = fmaxf(rm, fabsf(a.r[ray_index(G, it.view, it.u0 + k % wu, it.v0 + k / wu)]));
-    // non-negative floats order like their bit patterns
+    // non-negative floats order like their bit patterns; the warps' maxima
+    // meet in shared memory, so that the slot's word takes one atomic per CTA
+    // (a slot's thousands of CTA rows would otherwise queue on one address)
+    __shared__ unsigned s_m[kMaxBlock / 32];
     const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(rm));
-    if ((threadIdx.x & 31) == 0 && wm) atomicMax(a.rmax + it.slot, wm);
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = wm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned m = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_m[w]);
+        if (m) atomicMax(a.rmax + it.slot, m);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_slot_rmax(const TableArgs a,
