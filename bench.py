@@ -84,12 +84,13 @@ NCU_COUNTERS: dict = {
     #   k_forward_dual|k_epilogue" -s 10 -c 10 python bench.py --no-cpu --no-e2e --no-extras
     #   --steps 1 --warmup 3 --launch=-1,1  (GB300; mean of two batches of 12 slots);
     # the L2 figures from ncu --set full on the same command (-s 6 -c 3), taken
-    # with the same scatter code (the sources differed in the averaging kernel)
-    ("cone3d_256_360x384x384_360x64_g30", "4ee6fd6b5ebe15c6"): {
-        "backproject": {"traffic": 55567000, "issue_active_pct": 60.6,
+    # with the same scatter code (the sources differed in the averaging kernel
+    # and the max |r| pass)
+    ("cone3d_256_360x384x384_360x64_g30", "b53084ebfc2e142b"): {
+        "backproject": {"traffic": 55572000, "issue_active_pct": 60.8,
                         "lts_throughput_pct": 81.2, "l2_atomic_input_active_pct": 58.3,
                         "parts": "max |r| pass 14.6 MB + scatter 27.3 MB + conversion 13.6 MB"},
-        "forward_dual": {"traffic": 28037000, "issue_active_pct": 69.0},
+        "forward_dual": {"traffic": 28052000, "issue_active_pct": 69.0},
     },
 }
 KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/csrc/device.cuh",
