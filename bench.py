@@ -511,7 +511,8 @@ def run_gpu(args, cfg, world, rank, local):
         hbm_k["epoch_close"] = {"algorithmic_bytes_per_launch": b, "ms_per_launch": t * 1e3,
                                 "achieved_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
     roof["hbm_kernels"] = hbm_k
-    # the whole step against the same roof: SURVEY-style bytes 4 (2 R + 3 |J|) per step
+    # the whole step against the same roof: compulsory bytes 4 (2 R + 3 |J|) per step (r of the
+    # shadow rays in, z out, x_J in, x^_J in and out)
     step_bytes = 4 * (2 * rep["rays"] + 3 * rep["tile_voxels"]) * args.steps
     roof["step_bytes_gbs"] = step_bytes / (ms / 1e3) / 1e9
     # per batch: the backprojection (ray table + gather; max |r| pass + scatter +
