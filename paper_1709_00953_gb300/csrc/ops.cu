@@ -1707,9 +1707,18 @@ __device__ __forceinline__ void run_unit(const ExecTask& T, unsigned long long w
 
 constexpr int kExecThreads = 256;
 
+static_assert(sizeof(ExecTask) % 8 == 0 && alignof(ExecTask) >= 8, "8-byte copies of a task");
+constexpr int kTaskWords = (int)(sizeof(ExecTask) / 8);
+
 __global__ void __launch_bounds__(kExecThreads, 4) k_executor(const ExecArgs e) {
     __shared__ int s_task, s_p;
     __shared__ unsigned s_u, s_n;
+    // the claimed task's descriptor and arguments, copied into shared memory
+    // once per task: the bodies read their arguments from there (a stand-alone
+    // kernel has them in its parameter space) instead of from the task list
+    __shared__ unsigned long long s_tw[kTaskWords];
+    __shared__ int s_cached;
+    if (threadIdx.x == 0) s_cached = -1;
     // thread 0's state: the home problem (where the block last found work), the
     // chunk it claims there, and the chunk run last (counted as done before
     // the next claim)
@@ -1794,7 +1803,14 @@ __global__ void __launch_bounds__(kExecThreads, 4) k_executor(const ExecArgs e) 
         const int task = s_task;
         if (task == -2) return;
         if (task >= 0) {
-            const ExecTask& T = e.tasks[task];
+            if (task != s_cached) {
+                const unsigned long long* src =
+                    reinterpret_cast<const unsigned long long*>(e.tasks + task);
+                for (int i = threadIdx.x; i < kTaskWords; i += blockDim.x) s_tw[i] = src[i];
+                __syncthreads();
+                if (threadIdx.x == 0) s_cached = task;
+            }
+            const ExecTask& T = *reinterpret_cast<const ExecTask*>(s_tw);
             const unsigned u0 = s_u, n = s_n;
             for (unsigned w = u0; w < u0 + n; ++w) {
                 run_unit(T, w);
