@@ -280,7 +280,7 @@ def test_solver_parity(csgd, name, steps):
                                               ("cone_ragged", 30, 4), ("custom_sphere", 24, 2)])
 def test_scatter_backprojection_parity(csgd, name, steps, lanes):
     """The ray-driven scatter backprojection (each ray walks the tile and adds
-    len * r to 64-bit fixed-point sums with integer atomics) inside the solver:
+    len * r to 32-bit fixed-point sums with integer atomics) inside the solver:
     the same bounds against the oracle as the gather, the oracle's count of
     non-zeros, and the same result on a second run (order-independent sums)."""
     from oracle import blocks as OB
