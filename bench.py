@@ -83,14 +83,13 @@ NCU_COUNTERS: dict = {
     #   --clock-control none -k regex:"k_slot_rmax|k_backproject_scatter|k_scatter_convert|
     #   k_forward_dual|k_epilogue" -s 10 -c 10 python bench.py --no-cpu --no-e2e --no-extras
     #   --steps 1 --warmup 3 --launch=-1,1  (GB300; mean of two batches of 12 slots);
-    # the L2 figures from ncu --set full on the same command (-s 6 -c 3), taken
-    # with the same scatter code (the sources differed in the averaging kernel
-    # and the max |r| pass)
-    ("cone3d_256_360x384x384_360x64_g30", "b53084ebfc2e142b"): {
-        "backproject": {"traffic": 55572000, "issue_active_pct": 60.8,
-                        "lts_throughput_pct": 81.2, "l2_atomic_input_active_pct": 58.3,
+    # the L2 figures from ncu --set full -k regex:"k_forward_dual|k_backproject_scatter"
+    # -s 6 -c 2 on the same command
+    ("cone3d_256_360x384x384_360x64_g30", "1922eec259ea1d80"): {
+        "backproject": {"traffic": 55566000, "issue_active_pct": 60.0,
+                        "lts_throughput_pct": 82.0, "l2_atomic_input_active_pct": 58.8,
                         "parts": "max |r| pass 14.6 MB + scatter 27.3 MB + conversion 13.6 MB"},
-        "forward_dual": {"traffic": 28052000, "issue_active_pct": 69.0},
+        "forward_dual": {"traffic": 28032000, "issue_active_pct": 71.3},
     },
 }
 KERNEL_SOURCES = ("paper_1709_00953_gb300/csrc/ops.cu", "paper_1709_00953_gb300/csrc/device.cuh",

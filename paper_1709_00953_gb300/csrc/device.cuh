@@ -433,20 +433,21 @@ __device__ __forceinline__ void walk3_batched(const float q[3], const float inv[
             ln[u] = fmaxf(t - tc, 0.f);
             id[u] = idx;
             tc = t;
-            // only the axis whose plane is crossed advances (x, then y, on ties)
-            if (tn[0] == m) {
-                idx += ds[0];
-                p[0] += fs[0];
-                tn[0] = (p[0] - q[0]) * inv[0];
-            } else if (tn[1] == m) {
-                idx += ds[1];
-                p[1] += fs[1];
-                tn[1] = (p[1] - q[1]) * inv[1];
-            } else {
-                idx += ds[2];
-                p[2] += fs[2];
-                tn[2] = (p[2] - q[2]) * inv[2];
-            }
+            // only the axis whose plane is crossed advances (x, then y, on ties).
+            // Branch-free: the three candidate plane parameters are computed and
+            // the crossed axis's is selected (a branch diverges across the lanes
+            // of a warp, which cross different axes; an infinite or NaN
+            // candidate of an axis the line never crosses is never selected)
+            const bool cx = tn[0] == m, cy = !cx && tn[1] == m, cz = !cx && !cy;
+            idx += cx ? ds[0] : (cy ? ds[1] : ds[2]);
+            p[0] += cx ? fs[0] : 0.f;
+            p[1] += cy ? fs[1] : 0.f;
+            p[2] += cz ? fs[2] : 0.f;
+            const float n0 = (p[0] - q[0]) * inv[0], n1 = (p[1] - q[1]) * inv[1],
+                        n2 = (p[2] - q[2]) * inv[2];
+            tn[0] = cx ? n0 : tn[0];
+            tn[1] = cy ? n1 : tn[1];
+            tn[2] = cz ? n2 : tn[2];
         }
         f(id, ln);
     }
