@@ -373,9 +373,9 @@ int32_t csgd_batch_destroy(csgd_batch* batch);
  * the library's model (gather, occupancy-based groups, lanes by ray count).
  * They change only the rounding of the sums, i.e. results at rounding level.
  *   csgd_solver_set_launch: sets them; CSGD_ERR_INVALID_ARG out of range.
- *   csgd_solver_autotune: times the backprojection for every group count and
- *     the scatter, then the dual forward (plus the scatter, if chosen) for
- *     every lane count over the first trial_steps
+ *   csgd_solver_autotune: times the backprojection for every group count, the
+ *     scatter and the three brick shapes, then the dual forward (plus the
+ *     scatter, if chosen) for every lane count over the first trial_steps
  *     steps of the schedule (kernel time by CUDA events), keeps the fastest
  *     and resets the solver (x = 0, z = 0, r = y, schedule from the seed);
  *     writes the choice to bp_groups / fwd_lanes if non-NULL.  Synchronises. */
